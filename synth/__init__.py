@@ -1,0 +1,257 @@
+"""Seeded synthetic input generators.
+
+This module builds the sparse matrices, vectors, permutations and random labels
+that both the CPU oracle and the CUDA path are fed.  It holds none of the
+method's arithmetic: no SpMV, no form derivation, no connectivity counting, no
+partitioning.  Every generator returns plain numpy arrays:
+
+    rowptr  int32[m+1]   CSR row starts
+    colidx  int32[nnz]   column indices, sorted and unique within each row
+    vals    float64[nnz] values
+
+Workload recipes (the paper's 17 University of Florida matrices are not
+available; these families span the same regimes of row/column irregularity as
+Table 1 of the paper):
+
+* ``zipf_matrix``: 16,384^2, row degree d ~ P(d) proportional to d^-1.7498 on
+  [1, 512] (mean 8.000, max 512), columns drawn from a Zipf(s=1.2) law over a
+  seeded random permutation of the columns, without replacement inside a row.
+* ``mesh5``: 5-point stencil on an nx x nx grid, values U(-1,1), symmetric
+  random permutation.
+* ``rmat``: R-MAT (a,b,c,d) = (.57,.19,.19,.05) on 2^scale vertices, exactly
+  deg * 2^scale distinct (i,j) pairs, values U(-1,1).
+* ``blocks``: nb diagonal bs x bs blocks at a given fill plus a fraction of
+  random off-block nonzeros, symmetric random permutation.
+* ``laplacian3d``: 7-point Dirichlet Laplacian on an n^3 grid (6 / -1),
+  optionally symmetrically permuted (stays SPD).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "coo_to_csr", "zipf_matrix", "mesh5", "rmat", "blocks", "laplacian3d",
+    "random_perm", "uniform_x", "integer_x", "integer_values", "random_labels",
+    "random_sparse", "symmetric_permute", "csr_to_dense",
+]
+
+
+def _rng(seed):
+    return np.random.default_rng(np.random.SeedSequence(int(seed)))
+
+
+def coo_to_csr(m, n, rows, cols, vals):
+    """Assemble CSR from COO triplets with unique (row, col) pairs."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    key = rows * np.int64(n) + cols
+    order = np.argsort(key, kind="stable")
+    key_sorted = key[order]
+    if key_sorted.size > 1 and np.any(key_sorted[1:] == key_sorted[:-1]):
+        raise ValueError("duplicate (row, col) pair in COO input")
+    r = rows[order]
+    counts = np.bincount(r, minlength=m)
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    if rowptr[-1] >= 2**31:
+        raise ValueError("nnz does not fit int32 row pointers")
+    return (rowptr.astype(np.int32), cols[order].astype(np.int32),
+            vals[order].copy())
+
+
+def csr_to_dense(m, n, rowptr, colidx, vals):
+    a = np.zeros((m, n), dtype=np.float64)
+    for i in range(m):
+        for p in range(rowptr[i], rowptr[i + 1]):
+            a[i, colidx[p]] += vals[p]
+    return a
+
+
+def random_perm(n, seed):
+    return _rng(seed).permutation(n).astype(np.int32)
+
+
+def symmetric_permute(m, rowptr, colidx, vals, perm):
+    """Return P A P^T in CSR, where perm maps new index -> old index."""
+    perm = np.asarray(perm, dtype=np.int64)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size, dtype=np.int64)
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rowptr))
+    return coo_to_csr(m, m, inv[rows], inv[colidx.astype(np.int64)], vals)
+
+
+def uniform_x(n, seed, nrhs=1):
+    x = _rng(seed).uniform(-1.0, 1.0, size=(n, nrhs) if nrhs > 1 else n)
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def integer_x(n, seed, nrhs=1, lo=-8, hi=8):
+    x = _rng(seed).integers(lo, hi + 1, size=(n, nrhs) if nrhs > 1 else n)
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def integer_values(nnz, seed, lo=-8, hi=8):
+    """Small nonzero integers, so that every FP64 sum of products is exact."""
+    v = _rng(seed).integers(lo, hi, size=nnz).astype(np.float64)
+    v[v >= 0] += 1.0          # map [lo, hi) onto [lo, hi] without 0
+    return v
+
+
+def random_labels(count, K, seed, border_frac=0.0):
+    """Uniform labels in [0, K); with border_frac > 0 a fraction get label K."""
+    rng = _rng(seed)
+    lab = rng.integers(0, K, size=count).astype(np.int32)
+    if border_frac > 0:
+        lab[rng.random(count) < border_frac] = K
+    return lab
+
+
+def random_sparse(m, n, density, seed, integer=True, empty_rows=0.0):
+    """Small random CSR matrix (tests).  Optionally leaves some rows empty."""
+    rng = _rng(seed)
+    mask = rng.random((m, n)) < density
+    if empty_rows > 0:
+        mask[rng.random(m) < empty_rows, :] = False
+    r, c = np.nonzero(mask)
+    if integer:
+        v = integer_values(r.size, seed + 7919)
+    else:
+        v = rng.uniform(-1.0, 1.0, size=r.size)
+    return coo_to_csr(m, n, r, c, v)
+
+
+def zipf_matrix(m=16384, n=16384, seed=0, s_rows=1.7498, dmax=512, s_cols=1.2):
+    """Power-law rows (mean 8, max 512) with Zipf-distributed columns."""
+    rng = _rng(seed)
+    d = np.arange(1, dmax + 1, dtype=np.float64)
+    pd = d ** -s_rows
+    pd /= pd.sum()
+    deg = rng.choice(np.arange(1, dmax + 1), size=m, p=pd)
+    ranks = np.arange(1, n + 1, dtype=np.float64)
+    pc = ranks ** -s_cols
+    cdf = np.cumsum(pc / pc.sum())
+    cdf[-1] = 1.0
+    colperm = rng.permutation(n)
+    rows_out, cols_out = [], []
+    for i in range(m):
+        want = int(min(deg[i], n))
+        chosen = np.empty(0, dtype=np.int64)
+        while chosen.size < want:
+            draw = np.searchsorted(cdf, rng.random(2 * (want - chosen.size) + 8),
+                                   side="right")
+            allc = np.concatenate([chosen, draw])
+            _, first = np.unique(allc, return_index=True)
+            chosen = allc[np.sort(first)][:want]
+        rows_out.append(np.full(want, i, dtype=np.int64))
+        cols_out.append(colperm[chosen])
+    rows = np.concatenate(rows_out)
+    cols = np.concatenate(cols_out)
+    vals = rng.uniform(-1.0, 1.0, size=rows.size)
+    return coo_to_csr(m, n, rows, cols, vals)
+
+
+def mesh5(nx=1024, seed=0, permute=True):
+    """5-point stencil on an nx x nx grid, values U(-1,1)."""
+    rng = _rng(seed)
+    N = nx * nx
+    idx = np.arange(N, dtype=np.int64)
+    gx, gy = idx % nx, idx // nx
+    rows, cols = [idx], [idx]
+    for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+        ok = (gx + dx >= 0) & (gx + dx < nx) & (gy + dy >= 0) & (gy + dy < nx)
+        rows.append(idx[ok])
+        cols.append(idx[ok] + dx + dy * nx)
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = rng.uniform(-1.0, 1.0, size=rows.size)
+    if permute:
+        perm = rng.permutation(N)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(N)
+        rows, cols = inv[rows], inv[cols]
+    return coo_to_csr(N, N, rows, cols, vals)
+
+
+def rmat(scale=20, deg=16, a=0.57, b=0.19, c=0.19, seed=0, chunk=1 << 22):
+    """R-MAT graph with exactly deg * 2^scale distinct directed pairs."""
+    rng = _rng(seed)
+    n = 1 << scale
+    target = deg * n
+    keys = np.empty(0, dtype=np.int64)
+    ab, abc = a + b, a + b + c
+    while True:
+        i = np.zeros(chunk, dtype=np.int64)
+        j = np.zeros(chunk, dtype=np.int64)
+        for _ in range(scale):
+            u = rng.random(chunk)
+            bi = (u >= ab).astype(np.int64)
+            bj = (((u >= a) & (u < ab)) | (u >= abc)).astype(np.int64)
+            i = (i << 1) | bi
+            j = (j << 1) | bj
+        keys = np.concatenate([keys, (i << scale) | j])
+        uniq, first = np.unique(keys, return_index=True)
+        if uniq.size >= target:
+            keep = np.sort(first)[:target]
+            keys = keys[keep]
+            break
+        keys = keys[np.sort(first)]
+    rows, cols = keys >> scale, keys & (n - 1)
+    vals = rng.uniform(-1.0, 1.0, size=rows.size)
+    return coo_to_csr(n, n, rows, cols, vals)
+
+
+def blocks(nb=64, bs=16384, fill=0.002, border_frac=0.05, seed=0, permute=True):
+    """nb diagonal bs x bs blocks at `fill`, plus border_frac * (block nnz)
+    random off-block nonzeros, symmetrically permuted."""
+    rng = _rng(seed)
+    N = nb * bs
+    per_block = int(round(fill * bs * bs))
+    keys = []
+    for blk in range(nb):
+        got = np.empty(0, dtype=np.int64)
+        while got.size < per_block:
+            draw = rng.integers(0, bs * bs, size=int(1.02 * (per_block - got.size)) + 64)
+            got = np.unique(np.concatenate([got, draw]))
+        got = got[np.sort(rng.permutation(got.size)[:per_block])]
+        r, cc = got // bs + blk * bs, got % bs + blk * bs
+        keys.append(r * N + cc)
+    n_border = int(round(border_frac * per_block * nb))
+    bkeys = np.empty(0, dtype=np.int64)
+    while bkeys.size < n_border:
+        r = rng.integers(0, N, size=int(1.1 * (n_border - bkeys.size)) + 64)
+        cc = rng.integers(0, N, size=r.size)
+        off = (r // bs) != (cc // bs)
+        bkeys = np.unique(np.concatenate([bkeys, r[off] * N + cc[off]]))
+    bkeys = bkeys[np.sort(rng.permutation(bkeys.size)[:n_border])]
+    allk = np.concatenate(keys + [bkeys])
+    rows, cols = allk // N, allk % N
+    vals = rng.uniform(-1.0, 1.0, size=rows.size)
+    if permute:
+        perm = rng.permutation(N)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(N)
+        rows, cols = inv[rows], inv[cols]
+    return coo_to_csr(N, N, rows, cols, vals)
+
+
+def laplacian3d(n=128, seed=0, permute=True):
+    """7-point Dirichlet Laplacian on an n^3 grid: 6 on the diagonal, -1 to
+    each in-grid neighbour."""
+    N = n * n * n
+    idx = np.arange(N, dtype=np.int64)
+    gx, gy, gz = idx % n, (idx // n) % n, idx // (n * n)
+    rows, cols, vals = [idx], [idx], [np.full(N, 6.0)]
+    for d, g in ((1, gx), (n, gy), (n * n, gz)):
+        for s in (-1, 1):
+            ok = (g + s >= 0) & (g + s < n)
+            rows.append(idx[ok])
+            cols.append(idx[ok] + s * d)
+            vals.append(np.full(int(ok.sum()), -1.0))
+    rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    if permute:
+        perm = _rng(seed).permutation(N)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(N)
+        rows, cols = inv[rows], inv[cols]
+    return coo_to_csr(N, N, rows, cols, vals)
