@@ -1,0 +1,268 @@
+/*
+ * spmv.h -- C ABI of the GB300 cache-size-aware SpMV library.
+ *
+ * The library computes the repeated sparse matrix-vector product y <- A x of
+ * Akbudak, Kayaaslan and Aykanat ("Analyzing and enhancing OSKI for sparse
+ * matrix-vector multiplication") on sm_103a, in three forms of A:
+ *
+ *   - the K-way singly-bordered form A_SB = P_r A P_c (Sec. 3.1, eqs. 1-3),
+ *   - the K-way doubly-bordered form A_DB (Sec. 3.2, eq. 5),
+ *   - a nonzero-disjoint split A = A^1 + ... + A^K evaluated as the sequence
+ *     y <- y + A^k x (Sec. 4),
+ *
+ * plus the plain natural-order CSR product (Sec. 2.1) as the baseline.  The
+ * reorderings and splits come from the host-side recursive hypergraph
+ * bisection of Sec. 3.1 (column-net model), Sec. 3.2 (enhanced
+ * row-column-net model) and Sec. 4.1 (row-column-net model), or from the
+ * caller.
+ *
+ * Conventions for every call:
+ *   - Indices are int32 and 0-based.  Permutations map NEW -> OLD:
+ *     row_perm[i'] is the original row placed at position i'.
+ *   - spmv_exec works in the permuted space (x_hat = x P_c, y_hat = P_r y,
+ *     Sec. 3): an iterative solver stays there; spmv_permute_x and
+ *     spmv_unpermute_y move vectors in and out.
+ *   - Host pointers are read during the call only; nothing is retained.
+ *     Device pointers are plain CUDA device addresses on the current device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it; the call returns before the
+ *     work completes unless stated otherwise.
+ *   - No exception crosses the ABI.  Every call returns spmv_status; on
+ *     failure spmv_last_error() gives a thread-local message naming the
+ *     offending index.
+ *   - A plan is not thread-safe: calls on one plan must not overlap (two
+ *     spmv_exec of one plan on different streams race on its scratch).
+ */
+#ifndef SPMV_H
+#define SPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spmv_status {
+    SPMV_OK = 0,
+    SPMV_E_INVALID = 1,      /* malformed argument (bad CSR, size, dtype, NULL) */
+    SPMV_E_STRUCTURE = 2,    /* perm not a bijection, or a nonzero outside the
+                                blocks and borders of the declared form */
+    SPMV_E_NOMEM = 3,        /* device or host allocation failed */
+    SPMV_E_CUDA = 4,         /* a CUDA runtime call or launch failed */
+    SPMV_E_TIMEOUT = 5,      /* a bounded device wait gave up */
+    SPMV_E_UNSUPPORTED = 6,  /* valid request outside what the library builds */
+    SPMV_E_INTERNAL = 7      /* broken internal invariant (a bug) */
+} spmv_status;
+
+/* value / vector precisions (not in the paper, which uses FP64, Sec. 5.2):
+ * F64: values, x, y and accumulation in FP64.
+ * F32: values, x, y and accumulation in FP32.
+ * BF16: values in BF16, x, y and accumulation in FP32.
+ * Values are rounded to nearest-even from the FP64 master values. */
+enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 };
+
+/* forms of A (Sec. 2.1, 3.1, 3.2, 4) */
+enum { SPMV_NATURAL = 0, SPMV_SB = 1, SPMV_DB = 2, SPMV_SPLIT = 3 };
+
+/* plan flags */
+enum {
+    SPMV_FLAG_NO_STAGING = 1,    /* never stage x in shared memory (ablation) */
+    SPMV_FLAG_TILED_NATURAL = 2  /* natural form through the tiled kernel
+                                    instead of the plain vector-per-row kernel */
+};
+
+/* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,
+ * colIndex = colidx, rowStart = rowptr).  rowptr has m+1 entries with
+ * rowptr[0] = 0 and rowptr[m] = nnz < 2^31; column indices are sorted and
+ * unique inside each row.  Values are the FP64 master copy. */
+typedef struct spmv_csr {
+    int32_t m, n;
+    int64_t nnz;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const double *vals;
+} spmv_csr;
+
+/* Row and column permutations (new -> old).  NULL = identity. */
+typedef struct spmv_perm {
+    const int32_t *row_perm;   /* m entries */
+    const int32_t *col_perm;   /* n entries */
+} spmv_perm;
+
+/* The form of P_r A P_c.
+ *   SB / DB (eqs. 1, 5): row_part_ptr and col_part_ptr have K+2 entries.
+ *     In the permuted space R_k = rows [row_part_ptr[k], row_part_ptr[k+1])
+ *     for k < K and R_B = [row_part_ptr[K], row_part_ptr[K+1]) (empty for SB);
+ *     C_k and C_B likewise from col_part_ptr.  Every nonzero of R_k must lie
+ *     in C_k or C_B; R_B is unrestricted.
+ *   SPLIT (Sec. 4): nz_part[p] in [0, K) is the part of the p-th nonzero of the
+ *     ORIGINAL CSR.  row_part_ptr / col_part_ptr (K+2 entries, may be NULL)
+ *     give each part's home rows / columns in the permuted space (as produced
+ *     by spmv_form_from_labels: rows and columns grouped by first-touching
+ *     part); they only guide the staging of x.
+ *   NATURAL: the struct may be NULL. */
+typedef struct spmv_splits {
+    int32_t form;
+    int32_t K;
+    const int32_t *row_part_ptr;
+    const int32_t *col_part_ptr;
+    const int32_t *nz_part;
+} spmv_splits;
+
+/* Plan options.  Zero-initialise and set what you need. */
+typedef struct spmv_opts {
+    int32_t dtype;        /* SPMV_F64 / SPMV_F32 / SPMV_BF16 */
+    int32_t nrhs;         /* right-hand sides r: X is n x r, Y is m x r, row
+                             major; r in {1, 2, 4, 8} (0 = 1) */
+    int32_t tile_cols;    /* max x entries staged per tile (0 = default) */
+    int32_t tile_nnz;     /* target nonzeros per tile (0 = default) */
+    int32_t long_row;     /* rows longer than this are reduced in chunks by
+                             several CTAs (0 = default) */
+    int32_t lanes;        /* threads cooperating on one row: 2, 4, 8, 16 or 32
+                             (0 = chosen from the mean row length) */
+    int32_t flags;        /* SPMV_FLAG_* */
+    /* optional device allocator for plan-owned memory (NULL = cudaMalloc) */
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*release)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} spmv_opts;
+
+typedef struct spmv_plan spmv_plan;
+
+/* What a plan holds and moves, for measurement and tests. */
+typedef struct spmv_plan_info {
+    int32_t m, n;
+    int64_t nnz;
+    int32_t form, K, dtype, nrhs;
+    int32_t lanes;              /* threads per row in the row kernels */
+    int32_t tile_cols;          /* staging capacity per tile (x entries) */
+    int32_t n_tiles, n_staged_tiles, n_global_tiles, n_chunk_tiles;
+    int32_t launches_per_exec;  /* kernel launches one spmv_exec makes */
+    int32_t smem_bytes;         /* dynamic shared memory per CTA */
+    int64_t staged_entries;     /* x entries staged per exec, summed over tiles */
+    int64_t list_entries;       /* of which gathered through an index list */
+    int64_t partial_slots;      /* partial sums written per exec (split rows
+                                   shared by parts, chunks of long rows) */
+    int64_t fixup_rows;         /* rows finished by the fix-up kernel */
+    int64_t device_bytes;       /* plan-owned device memory */
+    int64_t compulsory_bytes;   /* nnz*(value+4) + (m+1)*4 + n*r*xb + m*r*yb */
+    int64_t moved_bytes;        /* bytes one exec reads/writes if every array
+                                   element it touches is moved once */
+} spmv_plan_info;
+
+/* Build a plan: validate A, the permutation and the form (eqs. 1, 2, 5 or
+ * Sec. 4), apply P_r A P_c, split per part, tile each part so its x working
+ * set fits one CTA's shared memory, convert values to opts->dtype, and upload
+ * everything to the current device.  Synchronous.  The plan owns its device
+ * memory (through opts->alloc when given).
+ * Errors: SPMV_E_INVALID (bad CSR or options), SPMV_E_STRUCTURE (bad perm,
+ * nonzero outside C_k and C_B, bad part pointers), SPMV_E_NOMEM, SPMV_E_CUDA. */
+spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm,
+                             const spmv_splits *splits, const spmv_opts *opts,
+                             spmv_plan **out);
+
+/* y_hat <- A_hat x_hat (Sec. 3), or y_hat <- 0; y_hat <- y_hat + A^k x_hat for
+ * k = 1..K (Sec. 4), on `stream`.  x_hat: n*r device elements, y_hat: m*r
+ * device elements (double for F64, float for F32/BF16), row major, no
+ * aliasing.  y_hat is overwritten.  Asynchronous. */
+spmv_status spmv_exec(spmv_plan *plan, const void *x_hat, void *y_hat, void *stream);
+
+/* spmv_exec with HOST x_hat / y_hat: copies x_hat in, runs, copies y_hat out
+ * and synchronises the stream before returning.  Device staging buffers are
+ * allocated on the first call and kept by the plan.  Pinned host memory makes
+ * the copies asynchronous DMA. */
+spmv_status spmv_exec_host(spmv_plan *plan, const void *x_hat_host, void *y_hat_host,
+                           void *stream);
+
+/* x_hat[j'] = x[col_perm[j']] and y[row_perm[i']] = y_hat[i'] (Sec. 3), on
+ * device memory, r values per entry.  Identity plans copy. */
+spmv_status spmv_permute_x(const spmv_plan *plan, const void *x, void *x_hat, void *stream);
+spmv_status spmv_unpermute_y(const spmv_plan *plan, const void *y_hat, void *y, void *stream);
+
+spmv_status spmv_plan_get_info(const spmv_plan *plan, spmv_plan_info *info);
+
+/* Release the plan and its device memory (synchronises the device first).
+ * NULL is accepted. */
+spmv_status spmv_plan_destroy(spmv_plan *plan);
+
+/* Derive a form from labels, on the host.
+ *   SPMV_SB: labels[m] in [0, K): rows ordered by (label, index); C_k = the
+ *     columns whose only part is k (lambda = 1, eq. 3), ordered by index;
+ *     C_B = columns with lambda >= 2 by index, then untouched columns.
+ *   SPMV_DB: labels[m] in [0, K]; label K puts the row in R_B (eq. 5);
+ *     lambda' counts non-border rows only.
+ *   SPMV_SPLIT: labels[nnz] in [0, K) per nonzero of the original CSR; rows
+ *     and columns ordered by the first part (smallest k) touching them,
+ *     untouched ones last, ties by index.
+ * Outputs (caller-allocated): row_perm[m], col_perm[n], row_part_ptr[K+2],
+ * col_part_ptr[K+2] in the layout of spmv_splits. */
+spmv_status spmv_form_from_labels(const spmv_csr *A, int32_t form, int32_t K,
+                                  const int32_t *labels, int32_t *row_perm,
+                                  int32_t *col_perm, int32_t *row_part_ptr,
+                                  int32_t *col_part_ptr);
+
+/* Hypergraph models for spmv_partition */
+enum {
+    SPMV_PART_CN = 0,     /* column-net model, connectivity metric -> SB
+                             (sHP_CN, Sec. 3.1) */
+    SPMV_PART_ERCN = 1,   /* enhanced row-column-net model: column nets cost 1
+                             with the connectivity metric (cut-net splitting),
+                             row nets cost nnz(r_i) with the cut-net metric
+                             (cut-net removal) -> DB (sHP_eRCN, Sec. 3.2) */
+    SPMV_PART_RCN = 2,    /* row-column-net model, connectivity metric on
+                             both net types -> split (mHP_RCN, Sec. 4.1) */
+    SPMV_PART_RANDOM = 3  /* uniform random row labels -> SB (a baseline) */
+};
+
+/* Stop rule of the recursive bisection (Sec. 5.1) */
+enum {
+    SPMV_FIT_CSR = 0,     /* part's CSR storage + x + y subvectors < part_bytes
+                             (FP64 values, int32 indices; the paper's rule) */
+    SPMV_FIT_X = 1        /* part's x subvector (8 bytes per column it touches;
+                             plus its y subvector for RCN) < part_bytes: the
+                             shared-memory adaptation */
+};
+
+typedef struct spmv_partition_opts {
+    int32_t method;       /* SPMV_PART_* */
+    int32_t K;            /* > 0: bisect to depth log2(K) (K a power of two) */
+    int64_t part_bytes;   /* K == 0: bisect until every part fits */
+    int32_t fit_rule;     /* SPMV_FIT_* */
+    int32_t threads;      /* host threads (0 = hardware concurrency) */
+    double imbalance;     /* allowed imbalance per bisection (0 = 0.10) */
+    uint64_t seed;
+} spmv_partition_opts;
+
+/* Output of spmv_partition; arrays are allocated by the library and released
+ * by spmv_partition_free. */
+typedef struct spmv_partition_out {
+    int32_t form;         /* SPMV_SB, SPMV_DB or SPMV_SPLIT */
+    int32_t K;            /* number of parts */
+    int32_t n_labels;     /* m (SB, DB) or nnz (SPLIT) */
+    int32_t *labels;      /* row labels (DB: K = row border) or nonzero labels */
+    int32_t *row_perm, *col_perm, *row_part_ptr, *col_part_ptr;
+    int64_t cost;         /* the partitioner's own accounting of the bound:
+                             eq. 4 for CN, eq. 6 for eRCN, eq. 7 for RCN */
+    int64_t cost_cols;    /* column share of cost (lambda sums over columns) */
+    int64_t cost_rows;    /* row share (RCN: sum lambda(r_i); eRCN: nnz(R_B)) */
+    double seconds;       /* wall time */
+} spmv_partition_out;
+
+/* Recursive hypergraph bisection of A under a model (Sec. 3.1, 3.2, 4.1,
+ * 5.1), host-only.  Deterministic for a given seed and thread count.
+ * Returns labels and the derived form (as spmv_form_from_labels).
+ * Errors: SPMV_E_INVALID (bad CSR, K not a power of two, no stop rule),
+ * SPMV_E_NOMEM. */
+spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_opts *opts,
+                           spmv_partition_out *out);
+void spmv_partition_free(spmv_partition_out *out);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *spmv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMV_H */

@@ -1,0 +1,445 @@
+// C ABI entry points (include/spmv.h): plan life cycle, execution, vector
+// permutation.  Host arrays are built by spmv_plan.cpp; this file owns the
+// device memory and the launches.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "spmv_device.h"
+
+using namespace spmv;
+
+struct spmv_plan {
+    HostPlan hp;                  // metadata only after upload
+    DevPlan dp;
+    spmv_plan_info info{};
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+    int device = 0;
+    const int32_t *d_row_perm = nullptr;
+    const int32_t *d_col_perm = nullptr;
+    void *io_x = nullptr, *io_y = nullptr;
+    size_t xbytes = 0, ybytes = 0;
+};
+
+namespace {
+
+void *dev_alloc(spmv_plan *p, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (p->alloc) return p->alloc(bytes, p->ctx);
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return ptr;
+}
+
+void dev_free(spmv_plan *p, void *ptr)
+{
+    if (!ptr) return;
+    if (p->release) p->release(ptr, p->ctx);
+    else cudaFree(ptr);
+}
+
+spmv_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return SPMV_E_CUDA;
+}
+
+// Carves typed sub-arrays out of one allocation (256-byte aligned each).
+struct Arena {
+    struct Item {
+        const void *host;
+        size_t bytes;
+        void **slot;
+    };
+    std::vector<Item> items;
+    size_t total = 0;
+    void add(const void *host, size_t bytes, void **slot)
+    {
+        items.push_back({host, bytes, slot});
+        total += (bytes + 255) & ~size_t(255);
+    }
+};
+
+template <class T>
+void add_vec(Arena &a, const std::vector<T> &v, const void **slot)
+{
+    a.add(v.data(), v.size() * sizeof(T), const_cast<void **>(slot));
+}
+
+spmv_status device_matches(const spmv_plan *p)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) {
+        set_error("plan was built on device %d, current device is %d", p->device, dev);
+        return SPMV_E_INVALID;
+    }
+    return SPMV_OK;
+}
+
+cudaError_t run(const spmv_plan *p, const void *x, void *y, cudaStream_t s)
+{
+    switch (p->hp.dtype) {
+    case SPMV_F64: return exec_f64(p->dp, x, y, s);
+    case SPMV_F32: return exec_f32(p->dp, x, y, s);
+    default: return exec_bf16(p->dp, x, y, s);
+    }
+}
+
+}  // namespace
+
+extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm,
+                                        const spmv_splits *splits, const spmv_opts *opts,
+                                        spmv_plan **out)
+{
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return SPMV_E_INVALID;
+    }
+    *out = nullptr;
+    spmv_plan *p = nullptr;
+    try {
+        p = new spmv_plan();
+        spmv_status st = build_host_plan(A, perm, splits, opts, &p->hp);
+        if (st != SPMV_OK) {
+            delete p;
+            return st;
+        }
+        if (opts && (opts->alloc || opts->release)) {
+            if (!opts->alloc || !opts->release) {
+                set_error("alloc and release must be given together");
+                delete p;
+                return SPMV_E_INVALID;
+            }
+            p->alloc = opts->alloc;
+            p->release = opts->release;
+            p->ctx = opts->alloc_ctx;
+        }
+        cudaError_t e = cudaGetDevice(&p->device);
+        if (e != cudaSuccess) {
+            delete p;
+            return cuda_fail(e, "cudaGetDevice");
+        }
+        HostPlan &hp = p->hp;
+        DevPlan &dp = p->dp;
+        const int vb = hp.dtype == SPMV_F64 ? 8 : (hp.dtype == SPMV_F32 ? 4 : 2);
+        const int xb = hp.dtype == SPMV_F64 ? 8 : 4;
+        const int r = hp.nrhs;
+
+        // values in the plan's precision (round to nearest even from FP64)
+        std::vector<double> v64;
+        std::vector<float> v32;
+        std::vector<uint16_t> v16;
+        const void *vhost = nullptr;
+        size_t vbytes = (size_t)hp.nnz * vb;
+        if (hp.dtype == SPMV_F64) {
+            vhost = hp.val.data();
+        } else if (hp.dtype == SPMV_F32) {
+            v32.resize((size_t)hp.nnz);
+            for (int64_t q = 0; q < hp.nnz; ++q) v32[q] = (float)hp.val[q];
+            vhost = v32.data();
+        } else {
+            v16.resize((size_t)hp.nnz);
+            for (int64_t q = 0; q < hp.nnz; ++q) v16[q] = bf16_rne(hp.val[q]);
+            vhost = v16.data();
+        }
+
+        const bool tiled = !hp.use_k1;
+        const bool any_staged = tiled && hp.n_staged_tiles > 0;
+        Arena a;
+        add_vec(a, hp.rowptr, (const void **)&dp.rowptr);
+        add_vec(a, hp.col32, (const void **)&dp.col32);
+        a.add(vhost, vbytes, const_cast<void **>(&dp.val));
+        if (any_staged) add_vec(a, hp.col16, (const void **)&dp.col16);
+        if (!tiled && !hp.long_rows.empty())
+            add_vec(a, hp.long_rows, (const void **)&dp.long_rows);
+        if (tiled) {
+            add_vec(a, hp.tiles, (const void **)&dp.tiles);
+            if (!hp.xlist.empty()) add_vec(a, hp.xlist, (const void **)&dp.xlist);
+            if (!hp.dst.empty()) add_vec(a, hp.dst, (const void **)&dp.dst);
+            if (!hp.fixups.empty()) add_vec(a, hp.fixups, (const void **)&dp.fixups);
+            if (hp.partial_slots > 0)
+                a.add(nullptr, (size_t)hp.partial_slots * r * xb, &dp.partial);
+        }
+        if (!hp.row_perm.empty()) add_vec(a, hp.row_perm, (const void **)&p->d_row_perm);
+        if (!hp.col_perm.empty()) add_vec(a, hp.col_perm, (const void **)&p->d_col_perm);
+
+        p->arena_bytes = a.total;
+        p->arena = dev_alloc(p, a.total);
+        if (!p->arena) {
+            set_error("device allocation of %zu bytes failed", a.total);
+            delete p;
+            return SPMV_E_NOMEM;
+        }
+        size_t off = 0;
+        for (auto &it : a.items) {
+            char *d = static_cast<char *>(p->arena) + off;
+            *it.slot = d;
+            if (it.host && it.bytes) {
+                e = cudaMemcpy(d, it.host, it.bytes, cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    spmv_status s = cuda_fail(e, "upload");
+                    spmv_plan_destroy(p);
+                    return s;
+                }
+            }
+            off += (it.bytes + 255) & ~size_t(255);
+        }
+
+        dp.m = hp.m;
+        dp.n = hp.n;
+        dp.nrhs = r;
+        dp.lanes = hp.lanes;
+        dp.long_thresh = hp.long_thresh;
+        dp.use_k1 = hp.use_k1;
+        dp.n_long = (int32_t)hp.long_rows.size();
+        dp.n_tiles = (int32_t)hp.tiles.size();
+        dp.n_fixups = (int32_t)hp.fixups.size();
+        dp.smem_bytes = any_staged ? hp.tile_cols * r * xb : 0;
+
+        // info
+        spmv_plan_info &I = p->info;
+        I.m = hp.m;
+        I.n = hp.n;
+        I.nnz = hp.nnz;
+        I.form = hp.form;
+        I.K = hp.K;
+        I.dtype = hp.dtype;
+        I.nrhs = r;
+        I.lanes = hp.lanes;
+        I.tile_cols = hp.tile_cols;
+        I.n_tiles = dp.n_tiles;
+        I.n_staged_tiles = hp.n_staged_tiles;
+        I.n_global_tiles = hp.n_global_tiles;
+        I.n_chunk_tiles = hp.n_chunk_tiles;
+        I.launches_per_exec = hp.m == 0 ? 0 : (tiled ? (dp.n_tiles > 0) + (dp.n_fixups > 0) : 1);
+        I.smem_bytes = dp.smem_bytes;
+        I.staged_entries = hp.staged_entries;
+        I.list_entries = hp.list_entries;
+        I.partial_slots = hp.partial_slots;
+        I.fixup_rows = dp.n_fixups;
+        I.device_bytes = (int64_t)a.total;
+        I.compulsory_bytes = hp.nnz * (vb + 4) + ((int64_t)hp.m + 1) * 4 +
+                             (int64_t)hp.n * r * xb + (int64_t)hp.m * r * xb;
+        if (!tiled) {
+            I.moved_bytes = I.compulsory_bytes + (int64_t)dp.n_long * 4;
+        } else {
+            // every element touched once: values, indices (16-bit for staged
+            // tiles), plan row starts, tiles, staged x (+ list indices), x of
+            // global/chunk tiles (distinct columns), y, dst, partials, fix-ups
+            int64_t staged_nnz = 0;
+            std::vector<char> seen((size_t)hp.n, 0);
+            int64_t gdistinct = 0;
+            for (const Tile &t : hp.tiles) {
+                int32_t q0, q1;
+                if (t.kind == TILE_CHUNK) {
+                    q0 = t.r0;
+                    q1 = t.r1;
+                } else {
+                    q0 = hp.rowptr[t.r0];
+                    q1 = hp.rowptr[t.r1];
+                }
+                if (t.kind == TILE_STAGED) {
+                    staged_nnz += q1 - q0;
+                    continue;
+                }
+                for (int32_t q = q0; q < q1; ++q)
+                    if (!seen[hp.col32[q]]) {
+                        seen[hp.col32[q]] = 1;
+                        ++gdistinct;
+                    }
+            }
+            I.moved_bytes = hp.nnz * vb + staged_nnz * 2 + (hp.nnz - staged_nnz) * 4 +
+                            (int64_t)hp.rowptr.size() * 4 + (int64_t)hp.tiles.size() * 32 +
+                            hp.staged_entries * r * xb + hp.list_entries * 4 +
+                            gdistinct * r * xb + (int64_t)hp.m * r * xb +
+                            (int64_t)hp.dst.size() * 4 + hp.partial_slots * r * xb * 2 +
+                            (int64_t)hp.fixups.size() * 16;
+        }
+        p->xbytes = (size_t)hp.n * r * xb;
+        p->ybytes = (size_t)hp.m * r * xb;
+
+        // the host image is no longer needed
+        HostPlan meta;
+        meta.m = hp.m;
+        meta.n = hp.n;
+        meta.nnz = hp.nnz;
+        meta.form = hp.form;
+        meta.K = hp.K;
+        meta.dtype = hp.dtype;
+        meta.nrhs = hp.nrhs;
+        meta.lanes = hp.lanes;
+        meta.tile_cols = hp.tile_cols;
+        meta.long_thresh = hp.long_thresh;
+        meta.use_k1 = hp.use_k1;
+        p->hp = std::move(meta);
+        *out = p;
+        return SPMV_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory");
+        if (p) spmv_plan_destroy(p);
+        return SPMV_E_NOMEM;
+    } catch (...) {
+        set_error("internal error");
+        if (p) spmv_plan_destroy(p);
+        return SPMV_E_INTERNAL;
+    }
+}
+
+extern "C" spmv_status spmv_exec(spmv_plan *plan, const void *x_hat, void *y_hat, void *stream)
+{
+    clear_error();
+    if (!plan) {
+        set_error("plan is NULL");
+        return SPMV_E_INVALID;
+    }
+    if ((!x_hat && plan->info.n > 0) || (!y_hat && plan->info.m > 0)) {
+        set_error("NULL vector");
+        return SPMV_E_INVALID;
+    }
+    spmv_status st = device_matches(plan);
+    if (st != SPMV_OK) return st;
+    cudaError_t e = run(plan, x_hat, y_hat, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "spmv kernel launch");
+    return SPMV_OK;
+}
+
+extern "C" spmv_status spmv_exec_host(spmv_plan *plan, const void *x_hat_host, void *y_hat_host,
+                                      void *stream)
+{
+    clear_error();
+    if (!plan) {
+        set_error("plan is NULL");
+        return SPMV_E_INVALID;
+    }
+    if ((!x_hat_host && plan->xbytes) || (!y_hat_host && plan->ybytes)) {
+        set_error("NULL vector");
+        return SPMV_E_INVALID;
+    }
+    spmv_status st = device_matches(plan);
+    if (st != SPMV_OK) return st;
+    if (!plan->io_x) {
+        plan->io_x = dev_alloc(plan, plan->xbytes);
+        plan->io_y = dev_alloc(plan, plan->ybytes);
+        if (!plan->io_x || !plan->io_y) {
+            set_error("device allocation of the host-I/O buffers failed");
+            return SPMV_E_NOMEM;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(plan->io_x, x_hat_host, plan->xbytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of x to the device");
+    e = run(plan, plan->io_x, plan->io_y, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv kernel launch");
+    e = cudaMemcpyAsync(y_hat_host, plan->io_y, plan->ybytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of y to the host");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return SPMV_OK;
+}
+
+static spmv_status permute_common(const spmv_plan *plan, const void *src, void *dst,
+                                  bool is_x, void *stream)
+{
+    clear_error();
+    if (!plan || !src || !dst) {
+        set_error("NULL argument");
+        return SPMV_E_INVALID;
+    }
+    spmv_status st = device_matches(plan);
+    if (st != SPMV_OK) return st;
+    const int xb = plan->info.dtype == SPMV_F64 ? 8 : 4;
+    const int32_t count = is_x ? plan->info.n : plan->info.m;
+    const int32_t *perm = is_x ? plan->d_col_perm : plan->d_row_perm;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (!perm) {
+        e = cudaMemcpyAsync(dst, src, (size_t)count * plan->info.nrhs * xb,
+                            cudaMemcpyDeviceToDevice, s);
+    } else {
+        e = permute_vector(xb, count, plan->info.nrhs, perm, src, dst, !is_x, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, is_x ? "permute x" : "unpermute y");
+    return SPMV_OK;
+}
+
+extern "C" spmv_status spmv_permute_x(const spmv_plan *plan, const void *x, void *x_hat,
+                                      void *stream)
+{
+    return permute_common(plan, x, x_hat, true, stream);
+}
+
+extern "C" spmv_status spmv_unpermute_y(const spmv_plan *plan, const void *y_hat, void *y,
+                                        void *stream)
+{
+    return permute_common(plan, y_hat, y, false, stream);
+}
+
+extern "C" spmv_status spmv_plan_get_info(const spmv_plan *plan, spmv_plan_info *info)
+{
+    clear_error();
+    if (!plan || !info) {
+        set_error("NULL argument");
+        return SPMV_E_INVALID;
+    }
+    *info = plan->info;
+    return SPMV_OK;
+}
+
+extern "C" spmv_status spmv_plan_destroy(spmv_plan *plan)
+{
+    clear_error();
+    if (!plan) return SPMV_OK;
+    cudaError_t e = cudaSuccess;
+    if (plan->arena || plan->io_x || plan->io_y) e = cudaDeviceSynchronize();
+    dev_free(plan, plan->io_x);
+    dev_free(plan, plan->io_y);
+    dev_free(plan, plan->arena);
+    delete plan;
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize before destroy");
+    return SPMV_OK;
+}
+
+// ------------------------------------------------------- permute kernels --
+namespace spmv {
+
+template <typename T>
+__global__ void k_permute(int64_t total, int32_t r, const int32_t *__restrict__ perm,
+                          const T *__restrict__ src, T *__restrict__ dst, bool scatter)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int64_t row = i / r, c = i - row * r;
+    const int64_t other = (int64_t)perm[row] * r + c;
+    if (scatter) dst[other] = src[i];
+    else dst[i] = src[other];
+}
+
+cudaError_t permute_vector(int elem_bytes, int32_t count, int32_t r, const int32_t *perm,
+                           const void *src, void *dst, bool scatter, cudaStream_t s)
+{
+    const int64_t total = (int64_t)count * r;
+    if (total == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (elem_bytes == 8)
+        k_permute<unsigned long long><<<blocks, 256, 0, s>>>(
+            total, r, perm, static_cast<const unsigned long long *>(src),
+            static_cast<unsigned long long *>(dst), scatter);
+    else
+        k_permute<unsigned int><<<blocks, 256, 0, s>>>(
+            total, r, perm, static_cast<const unsigned int *>(src),
+            static_cast<unsigned int *>(dst), scatter);
+    return cudaGetLastError();
+}
+
+}  // namespace spmv
