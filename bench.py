@@ -70,6 +70,9 @@ def build_forms(S, name, rp, ci, n, forms, seed=0, log=None):
         t0 = time.perf_counter()
         if f == "natural":
             out[f] = {}
+        elif f == "tiled":
+            # natural order through the tiled kernel
+            out[f] = dict(flags=S.SPMV_FLAG_TILED_NATURAL)
         elif f == "random":
             p = synth.random_perm(m, 1000 + seed)
             q = p if m == n else synth.random_perm(n, 2000 + seed)
@@ -90,10 +93,13 @@ def build_forms(S, name, rp, ci, n, forms, seed=0, log=None):
                                                              lab)
             out[f] = dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SPLIT, K=q * q,
                           row_part_ptr=rpp, col_part_ptr=cpp, nz_part=lab)
-        elif f in ("sb", "db"):
-            method = S.SPMV_PART_CN if f == "sb" else S.SPMV_PART_ERCN
-            res = S.spmv_partition(m, n, rp, ci, method, part_bytes=_part_bytes(f),
-                                   fit_rule=S.SPMV_FIT_X, seed=seed)
+        elif f[:2] in ("sb", "db") and f not in ("sbblock",):
+            method = S.SPMV_PART_CN if f.startswith("sb") else S.SPMV_PART_ERCN
+            if len(f) > 2:      # fixed K: bisect to depth log2(K)
+                res = S.spmv_partition(m, n, rp, ci, method, K=int(f[2:]), seed=seed)
+            else:               # size rule: bisect until the x subvector fits
+                res = S.spmv_partition(m, n, rp, ci, method, part_bytes=_part_bytes(f),
+                                       fit_rule=S.SPMV_FIT_X, seed=seed)
             out[f] = dict(row_perm=res["row_perm"], col_perm=res["col_perm"], form=res["form"],
                           K=res["K"], row_part_ptr=res["row_part_ptr"],
                           col_part_ptr=res["col_part_ptr"])

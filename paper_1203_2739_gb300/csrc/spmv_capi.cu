@@ -141,32 +141,36 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         std::vector<float> v32;
         std::vector<uint16_t> v16;
         const void *vhost = nullptr;
-        size_t vbytes = (size_t)hp.nnz * vb;
+        const size_t nelem = hp.val.size();        // stored elements (with padding)
+        size_t vbytes = nelem * vb;
         if (hp.dtype == SPMV_F64) {
             vhost = hp.val.data();
         } else if (hp.dtype == SPMV_F32) {
-            v32.resize((size_t)hp.nnz);
-            for (int64_t q = 0; q < hp.nnz; ++q) v32[q] = (float)hp.val[q];
+            v32.resize(nelem);
+            for (size_t q = 0; q < nelem; ++q) v32[q] = (float)hp.val[q];
             vhost = v32.data();
         } else {
-            v16.resize((size_t)hp.nnz);
-            for (int64_t q = 0; q < hp.nnz; ++q) v16[q] = bf16_rne(hp.val[q]);
+            v16.resize(nelem);
+            for (size_t q = 0; q < nelem; ++q) v16[q] = bf16_rne(hp.val[q]);
             vhost = v16.data();
         }
 
         const bool tiled = !hp.use_k1;
         const bool any_staged = tiled && hp.n_staged_tiles > 0;
         Arena a;
-        add_vec(a, hp.rowptr, (const void **)&dp.rowptr);
+        if (!tiled) add_vec(a, hp.rowptr, (const void **)&dp.rowptr);
         add_vec(a, hp.col32, (const void **)&dp.col32);
         a.add(vhost, vbytes, const_cast<void **>(&dp.val));
-        if (any_staged) add_vec(a, hp.col16, (const void **)&dp.col16);
+        if (tiled && hp.narrow_nnz > 0) add_vec(a, hp.col16, (const void **)&dp.col16);
         if (!tiled && !hp.long_rows.empty())
             add_vec(a, hp.long_rows, (const void **)&dp.long_rows);
         if (tiled) {
             add_vec(a, hp.tiles, (const void **)&dp.tiles);
+            add_vec(a, hp.chunk_off, (const void **)&dp.chunk_off);
+            add_vec(a, hp.slot_dst, (const void **)&dp.slot_dst);
+            add_vec(a, hp.slot_len, (const void **)&dp.slot_len);
+            if (!hp.vrows.empty()) add_vec(a, hp.vrows, (const void **)&dp.vrows);
             if (!hp.xlist.empty()) add_vec(a, hp.xlist, (const void **)&dp.xlist);
-            if (!hp.dst.empty()) add_vec(a, hp.dst, (const void **)&dp.dst);
             if (!hp.fixups.empty()) add_vec(a, hp.fixups, (const void **)&dp.fixups);
             if (hp.partial_slots > 0)
                 a.add(nullptr, (size_t)hp.partial_slots * r * xb, &dp.partial);
@@ -234,37 +238,51 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         if (!tiled) {
             I.moved_bytes = I.compulsory_bytes + (int64_t)dp.n_long * 4;
         } else {
-            // every element touched once: values, indices (16-bit for staged
-            // tiles), plan row starts, tiles, staged x (+ list indices), x of
-            // global/chunk tiles (distinct columns), y, dst, partials, fix-ups
-            int64_t staged_nnz = 0;
+            // every element touched once: values and indices (16-bit in narrow
+            // tiles) of the stored rows, chunk metadata, tiles, staged x (+ list
+            // indices), x read directly (distinct columns), y, partials, fix-ups
             std::vector<char> seen((size_t)hp.n, 0);
             int64_t gdistinct = 0;
-            for (const Tile &t : hp.tiles) {
-                int32_t q0, q1;
-                if (t.kind == TILE_CHUNK) {
-                    q0 = t.r0;
-                    q1 = t.r1;
-                } else {
-                    q0 = hp.rowptr[t.r0];
-                    q1 = hp.rowptr[t.r1];
+            auto see = [&](int32_t c) {
+                if (!seen[c]) {
+                    seen[c] = 1;
+                    ++gdistinct;
                 }
-                if (t.kind == TILE_STAGED) {
-                    staged_nnz += q1 - q0;
+            };
+            for (const Tile &t : hp.tiles) {
+                if (t.kind == TILE_CHUNK) {
+                    for (int32_t e = t.e0; e < t.e1; ++e) see(hp.col32[e]);
                     continue;
                 }
-                for (int32_t q = q0; q < q1; ++q)
-                    if (!seen[hp.col32[q]]) {
-                        seen[hp.col32[q]] = 1;
-                        ++gdistinct;
+                if (t.kind == TILE_NARROW) continue;
+                for (int32_t v = t.vrow0; v < t.vrow0 + t.nvrows; ++v)
+                    for (int32_t k = 0; k < hp.vrows[v].len; ++k) {
+                        const int32_t c = hp.col32[hp.vrows[v].e0 + k];
+                        if (t.kind == TILE_MIXED) {
+                            if (c < 0) see(~c);
+                        } else {
+                            see(c);
+                        }
+                    }
+                for (int32_t ch = t.chunk0; ch < t.chunk0 + t.nchunks; ++ch)
+                    for (int32_t i = 0; i < 32; ++i) {
+                        const int32_t len = hp.slot_len[ch * 32 + i];
+                        for (int32_t k = 0; k < len; ++k) {
+                            const int32_t c = hp.col32[hp.chunk_off[ch] + k * 32 + i];
+                            if (t.kind == TILE_MIXED) {
+                                if (c < 0) see(~c);
+                            } else {
+                                see(c);
+                            }
+                        }
                     }
             }
-            I.moved_bytes = hp.nnz * vb + staged_nnz * 2 + (hp.nnz - staged_nnz) * 4 +
-                            (int64_t)hp.rowptr.size() * 4 + (int64_t)hp.tiles.size() * 32 +
-                            hp.staged_entries * r * xb + hp.list_entries * 4 +
-                            gdistinct * r * xb + (int64_t)hp.m * r * xb +
-                            (int64_t)hp.dst.size() * 4 + hp.partial_slots * r * xb * 2 +
-                            (int64_t)hp.fixups.size() * 16;
+            I.moved_bytes = hp.nnz * vb + hp.narrow_nnz * 2 + (hp.nnz - hp.narrow_nnz) * 4 +
+                            (int64_t)hp.slot_dst.size() * 8 + (int64_t)hp.chunk_off.size() * 4 +
+                            (int64_t)hp.vrows.size() * 16 +
+                            (int64_t)hp.tiles.size() * 48 + hp.staged_entries * r * xb +
+                            hp.list_entries * 4 + gdistinct * r * xb + (int64_t)hp.m * r * xb +
+                            hp.partial_slots * r * xb * 2 + (int64_t)hp.fixups.size() * 16;
         }
         p->xbytes = (size_t)hp.n * r * xb;
         p->ybytes = (size_t)hp.m * r * xb;

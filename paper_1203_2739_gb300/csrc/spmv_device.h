@@ -19,12 +19,15 @@ struct DevPlan {
     int32_t n_long = 0;
     const Tile *tiles = nullptr;
     int32_t n_tiles = 0;
+    const int32_t *chunk_off = nullptr;
+    const int32_t *slot_dst = nullptr;
+    const int32_t *slot_len = nullptr;
+    const VRow *vrows = nullptr;
     const int32_t *xlist = nullptr;
-    const int32_t *dst = nullptr;
     void *partial = nullptr;
     const Fixup *fixups = nullptr;
     int32_t n_fixups = 0;
-    int32_t smem_bytes = 0;
+    int32_t smem_bytes = 0;            // staged x entries
 };
 
 cudaError_t exec_f64(const DevPlan &P, const void *x, void *y, cudaStream_t s);

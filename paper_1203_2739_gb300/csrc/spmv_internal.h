@@ -18,27 +18,47 @@ void clear_error();
 // ----------------------------------------------------------------- tiles --
 // A tile is the unit of work of one CTA in the tiled kernel.  It plays the
 // part the paper gives to a submatrix that "fits into the cache" (Sec. 3):
-// its whole x working set is staged in the CTA's shared memory.
+// the x entries it reuses are staged once in the CTA's shared memory; the
+// ones it touches only once are gathered straight from L2.
+//
+// Inside a tile the rows are sorted by length and cut into chunks of 32; a
+// chunk is stored column-major (element k of the chunk's 32 rows are 32
+// consecutive entries), so a warp handles 32 rows with one lane per row,
+// coalesced loads and one full-width FMA per stored element.  GB300 executes
+// two FP64 FMAs per SM per clock: an FP64 SpMV only keeps up with HBM when no
+// FP64 instruction runs with idle lanes and no shuffle reductions are needed.
 enum TileKind : int32_t {
-    TILE_STAGED = 0,   // rows [r0,r1), x entries staged in shared memory
-    TILE_GLOBAL = 1,   // rows [r0,r1), x gathered from global memory (L2)
-    TILE_CHUNK = 2     // nonzeros [r0,r1) of one long row -> partial slot y0
+    TILE_NARROW = 0,   // every nonzero reads staged x: 16-bit local indices (col16)
+    TILE_MIXED = 1,    // col32 >= 0: staged index; col32 < 0: ~global x index
+    TILE_GLOBAL = 2,   // col32 = global x index, nothing staged
+    TILE_CHUNK = 3     // elements [e0, e1) of one long row -> partial slot
 };
 
-struct Tile {          // 32 bytes, copied to the device as is
+struct Tile {          // 48 bytes, copied to the device as is
     int32_t kind;
-    int32_t r0, r1;    // plan rows (STAGED/GLOBAL) or nonzero range (CHUNK)
-    int32_t y0;        // >= 0: plan row r writes y[y0 + r - r0]; -1: via dst[r];
-                       // CHUNK: the partial slot it writes
-    int32_t run0, runlen;   // STAGED: x_hat[run0 + i] -> smem[i]
-    int32_t list0, listlen; // STAGED: x_hat[xlist[list0 + i]] -> smem[runlen + i]
+    int32_t chunk0, nchunks;  // chunks of 32 rows (not CHUNK tiles)
+    int32_t slot;             // CHUNK: the partial slot it writes
+    int32_t run0, runlen;     // x_hat[run0 + i] -> smem[i]
+    int32_t list0, listlen;   // x_hat[xlist[list0 + i]] -> smem[runlen + i]
+    int32_t e0, e1;           // CHUNK: element range (contiguous, global indices)
+    int32_t vrow0, nvrows;    // rows too long for one lane: vrows[vrow0 ..]
 };
-static_assert(sizeof(Tile) == 32, "Tile layout");
+static_assert(sizeof(Tile) == 48, "Tile layout");
+
+// A row of a tile reduced by a whole warp: elements [e0, e0 + len) stored
+// contiguously with the tile's index encoding; dst as slot_dst.
+struct VRow {
+    int32_t e0, len, dst, pad;
+};
+static_assert(sizeof(VRow) == 16, "VRow layout");
 
 struct Fixup {         // y[row] = sum of partial[slot0 .. slot0+count) in order
     int32_t row, slot0, count, pad;
 };
 static_assert(sizeof(Fixup) == 16, "Fixup layout");
+
+// slot_dst encoding: >= 0 y row; -1 empty slot; <= -2 partial slot -(d + 2)
+inline int32_t dst_partial(int32_t slot) { return -(slot + 2); }
 
 // Host image of a plan: every array the device needs, in device layout.
 struct HostPlan {
@@ -49,19 +69,25 @@ struct HostPlan {
     int32_t flags = 0;
     bool use_k1 = true;            // natural form: vector-per-row kernel
 
-    std::vector<int32_t> rowptr;   // K1: m+1; tiles: plan rows + 1
-    std::vector<int32_t> col32;    // global column (x_hat index) per nonzero
-    std::vector<uint16_t> col16;   // local shared-memory index (staged tiles)
-    std::vector<double> val;       // FP64 master values in plan order
+    // K1: CSR.  Tiled forms: elements in chunk order, then the long rows.
+    std::vector<int32_t> rowptr;   // K1 only
+    std::vector<int32_t> col32;    // K1 / GLOBAL / CHUNK: x index; MIXED: signed
+    std::vector<uint16_t> col16;   // NARROW tiles: shared-memory index
+    std::vector<double> val;       // FP64 master values in element order
     std::vector<int32_t> long_rows;  // K1: rows reduced by a whole CTA
 
     std::vector<Tile> tiles;
+    std::vector<int32_t> chunk_off;  // element offset of each chunk
+    std::vector<int32_t> slot_dst;   // 32 per chunk
+    std::vector<int32_t> slot_len;   // 32 per chunk (row length, 0 if empty)
+    std::vector<VRow> vrows;
     std::vector<int32_t> xlist;
-    std::vector<int32_t> dst;      // per plan row: y row, or -(slot+1)
     std::vector<Fixup> fixups;
     int64_t partial_slots = 0;
     int32_t n_chunk_tiles = 0, n_staged_tiles = 0, n_global_tiles = 0;
-    int64_t staged_entries = 0, list_entries = 0;
+    int64_t staged_entries = 0, list_entries = 0, direct_nnz = 0, narrow_nnz = 0;
+    int64_t padded_elems = 0;      // stored elements (with padding) in chunks
+    int64_t fma_slots = 0;         // sum over chunks of 32 * (longest row)
 
     std::vector<int32_t> row_perm, col_perm;  // empty = identity
 };

@@ -6,16 +6,18 @@
 //                     coalesced streaming of values and column indices
 //                     (evict-first), x gathered through the read-only path,
 //                     warp-shuffle reduction; rows longer than a threshold get
-//                     a whole CTA each.
+//                     a whole CTA each.  This is the baseline.
 //  * k_tiles       -- one CTA per tile of a part of the SB / DB form or of a
-//                     split (Sec. 3, Sec. 4).  A staged tile first copies its x
-//                     working set (a contiguous run of x plus an index list)
-//                     into shared memory, which is the "cache" the partition
-//                     was sized for, then reduces its rows against shared
-//                     memory with 16-bit local column indices.  Global tiles
-//                     (the DB row border R_B, tiles with no reuse) gather x
-//                     from L2.  Chunk tiles reduce a slice of one long row into
-//                     a partial sum.
+//                     split (Sec. 3, Sec. 4).  The tile first copies the x
+//                     entries it reuses into shared memory -- the "cache" the
+//                     partition was sized for -- then each warp takes chunks of
+//                     32 length-sorted rows stored column-major: one lane per
+//                     row, coalesced loads, one FMA chain per row.  No FP64
+//                     instruction runs with idle lanes for want of work and no
+//                     shuffle reduction is needed, which matters on GB300 where
+//                     FP64 issues at two FMAs per SM per clock.  Columns used
+//                     once by the tile are gathered from L2 directly.  Chunk
+//                     tiles reduce a slice of one long row into a partial sum.
 //  * k_fixup       -- rows with several contributions (split rows shared by
 //                     parts, chunked long rows) are summed from their partial
 //                     sums in part order: y <- y + A^k x accumulated on the fly
@@ -24,6 +26,10 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "spmv_device.h"
 
@@ -127,13 +133,18 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
 }
 
 // ----------------------------------------------------------- tiled kernel --
-template <int LANES, int R, typename VT, typename XT>
+// One CTA per tile.  After staging, warp w takes chunks w, w+8, ...; lane i
+// owns row i of the chunk and runs one FMA chain over its row: element k of
+// the chunk's rows sits at chunk_off + 32 k + i, so every load is coalesced
+// and every FP64 FMA runs with the lanes of all rows still going.
+template <int R, typename VT, typename XT>
 __global__ void __launch_bounds__(kThreads)
-k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ prp,
-        const uint16_t *__restrict__ c16, const int32_t *__restrict__ c32,
+k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
+        const int32_t *__restrict__ slot_dst, const int32_t *__restrict__ slot_len,
+        const VRow *__restrict__ vrows, const uint16_t *__restrict__ c16,
+        const int32_t *__restrict__ c32,
         const VT *__restrict__ val, const int32_t *__restrict__ xlist,
-        const int32_t *__restrict__ dst, const XT *__restrict__ x, XT *__restrict__ y,
-        XT *__restrict__ partial)
+        const XT *__restrict__ x, XT *__restrict__ y, XT *__restrict__ partial)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     XT *seg = reinterpret_cast<XT *>(smem_raw);
@@ -143,23 +154,23 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ prp,
         XT s[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) s[c] = XT(0);
-        for (int32_t p = t.r0 + (int32_t)threadIdx.x; p < t.r1; p += kThreads) {
-            const XT v = (XT)load_val(val + p);
-            const int64_t xc = (int64_t)__ldcs(c32 + p) * R;
+        for (int32_t e = t.e0 + (int32_t)threadIdx.x; e < t.e1; e += kThreads) {
+            const XT v = (XT)load_val(val + e);
+            const int64_t xc = (int64_t)__ldcs(c32 + e) * R;
 #pragma unroll
             for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
         }
         block_sum<R>(s);
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int c = 0; c < R; ++c) partial[(int64_t)t.y0 * R + c] = s[c];
+            for (int c = 0; c < R; ++c) partial[(int64_t)t.slot * R + c] = s[c];
         }
         return;
     }
 
-    const bool staged = (t.kind == TILE_STAGED);
-    if (staged) {
-        // stage the tile's x working set: the contiguous run, then the list
+    const int kind = t.kind;
+    if (kind != TILE_GLOBAL) {
+        // stage the reused x entries: the contiguous run, then the list
         for (int32_t i = threadIdx.x; i < t.runlen; i += kThreads) {
             const int64_t src = (int64_t)(t.run0 + i) * R;
 #pragma unroll
@@ -174,47 +185,85 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ prp,
         __syncthreads();
     }
 
-    constexpr int NG = kThreads / LANES;
-    const int g = threadIdx.x / LANES, lane = threadIdx.x & (LANES - 1);
-    for (int32_t rb = t.r0; rb < t.r1; rb += NG) {
-        const int32_t r = rb + g;
-        const bool valid = r < t.r1;
-        int32_t p0 = 0, p1 = 0;
-        if (valid) {
-            p0 = prp[r];
-            p1 = prp[r + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the x entry of element e for right-hand side c
+    auto xat = [&](int32_t ci, int c) -> XT {
+        if (kind == TILE_GLOBAL) return __ldg(x + (int64_t)ci * R + c);
+        if (ci >= 0) return seg[ci * R + c];
+        return __ldg(x + (int64_t)(~ci) * R + c);
+    };
+    auto colat = [&](int64_t e) -> int32_t {
+        return kind == TILE_NARROW ? (int32_t)__ldcs(c16 + e) : __ldcs(c32 + e);
+    };
+    auto store = [&](int32_t d, const XT (&s)[R]) {
+        if (d >= 0) {
+#pragma unroll
+            for (int c = 0; c < R; ++c) y[(int64_t)d * R + c] = s[c];
+        } else if (d <= -2) {
+            const int64_t ps = (int64_t)(-d - 2) * R;
+#pragma unroll
+            for (int c = 0; c < R; ++c) partial[ps + c] = s[c];
         }
+    };
+    constexpr int U = R == 1 ? 8 : (R == 2 ? 4 : 2);
+
+    // rows too long for one lane: a warp each, batches of U loads per lane
+    for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += kThreads / 32) {
+        const VRow row = vrows[vr];
         XT s[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) s[c] = XT(0);
-        if (staged) {
-            for (int32_t p = p0 + lane; p < p1; p += LANES) {
-                const XT v = (XT)load_val(val + p);
-                const int32_t l = (int32_t)__ldcs(c16 + p) * R;
+        for (int32_t k0 = 0; k0 < row.len; k0 += 32 * U) {
+            XT v[U];
+            int32_t ci[U];
 #pragma unroll
-                for (int c = 0; c < R; ++c) s[c] = fma(v, seg[l + c], s[c]);
+            for (int u = 0; u < U; ++u) {
+                const int32_t k = k0 + u * 32 + lane;
+                const bool on = k < row.len;
+                v[u] = on ? (XT)load_val(val + row.e0 + k) : XT(0);
+                ci[u] = on ? colat(row.e0 + k) : 0;
             }
-        } else {
-            for (int32_t p = p0 + lane; p < p1; p += LANES) {
-                const XT v = (XT)load_val(val + p);
-                const int64_t xc = (int64_t)__ldcs(c32 + p) * R;
 #pragma unroll
-                for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
+            for (int u = 0; u < U; ++u) {
+                if (k0 + u * 32 + lane < row.len) {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) s[c] = fma(v[u], xat(ci[u], c), s[c]);
+                }
             }
         }
 #pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = group_sum<LANES>(s[c]);
-        if (valid && lane == 0) {
-            XT *out;
-            if (t.y0 >= 0) {
-                out = y + (int64_t)(t.y0 + (r - t.r0)) * R;
-            } else {
-                const int32_t d = dst[r];
-                out = d >= 0 ? y + (int64_t)d * R : partial + (int64_t)(-d - 1) * R;
+        for (int c = 0; c < R; ++c) s[c] = group_sum<32>(s[c]);
+        if (lane == 0) store(row.dst, s);
+    }
+
+    // chunks of 32 rows, one lane per row, batches of U elements per lane
+    for (int32_t ch = t.chunk0 + warp; ch < t.chunk0 + t.nchunks; ch += kThreads / 32) {
+        const int32_t slot = ch * 32 + lane;
+        const int32_t len = __ldg(slot_len + slot);
+        const int32_t L = __shfl_sync(0xffffffffu, len, 0);   // rows sorted: lane 0 is longest
+        const int64_t off = __ldg(chunk_off + ch) + lane;
+        XT s[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) s[c] = XT(0);
+        for (int32_t k0 = 0; k0 < L; k0 += U) {
+            XT v[U];
+            int32_t ci[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool on = k0 + u < len;
+                const int64_t e = off + (int64_t)(k0 + u) * 32;
+                v[u] = on ? (XT)load_val(val + e) : XT(0);
+                ci[u] = on ? colat(e) : 0;
             }
 #pragma unroll
-            for (int c = 0; c < R; ++c) out[c] = s[c];
+            for (int u = 0; u < U; ++u) {
+                if (k0 + u < len) {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) s[c] = fma(v[u], xat(ci[u], c), s[c]);
+                }
+            }
         }
+        store(__ldg(slot_dst + slot), s);
     }
 }
 
@@ -236,40 +285,51 @@ k_fixup(const Fixup *__restrict__ f, const int32_t nf, const XT *__restrict__ pa
 }
 
 // ---------------------------------------------------------------- launcher --
-// Raise the dynamic shared memory limit of a kernel once per device.
+// Raise the dynamic shared memory limit of a kernel once per device (the
+// kernels also hold a little static shared memory, so the opt-in is needed
+// below 48 KB of dynamic memory too).
 template <class Kern>
 inline cudaError_t ensure_smem(Kern k, int bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    static int done_bytes[64] = {0};
+    if (bytes <= 0) return cudaSuccess;
+    // one cache per kernel instance (the template is shared by every kernel
+    // with the same signature, so the key is the kernel's address)
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 64 && done_bytes[dev] >= bytes) return cudaSuccess;
+    const auto key = std::make_pair(reinterpret_cast<const void *>(k), dev);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess && dev < 64) done_bytes[dev] = bytes;
+    if (e == cudaSuccess) done[key] = bytes;
     return e;
 }
 
 template <int LANES, int R, typename VT, typename XT>
-cudaError_t launch_fixed(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
+cudaError_t launch_k1(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
 {
-    if (P.use_k1) {
-        constexpr int rows_per_block = kThreads / LANES;
-        const int64_t nb = ((int64_t)P.m + rows_per_block - 1) / rows_per_block + P.n_long;
-        if (nb > 0)
-            k_csr_vector<LANES, R, VT, XT><<<(unsigned)nb, kThreads, 0, s>>>(
-                P.m, P.rowptr, P.col32, static_cast<const VT *>(P.val), x, y, P.long_rows,
-                P.n_long, P.long_thresh);
-        return cudaGetLastError();
-    }
+    constexpr int rows_per_block = kThreads / LANES;
+    const int64_t nb = ((int64_t)P.m + rows_per_block - 1) / rows_per_block + P.n_long;
+    if (nb > 0)
+        k_csr_vector<LANES, R, VT, XT><<<(unsigned)nb, kThreads, 0, s>>>(
+            P.m, P.rowptr, P.col32, static_cast<const VT *>(P.val), x, y, P.long_rows, P.n_long,
+            P.long_thresh);
+    return cudaGetLastError();
+}
+
+template <int R, typename VT, typename XT>
+cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
+{
     if (P.n_tiles > 0) {
-        auto kern = k_tiles<LANES, R, VT, XT>;
+        auto kern = k_tiles<R, VT, XT>;
         cudaError_t e = ensure_smem(kern, P.smem_bytes);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)P.n_tiles, kThreads, P.smem_bytes, s>>>(
-            P.tiles, P.rowptr, P.col16, P.col32, static_cast<const VT *>(P.val), P.xlist, P.dst,
-            x, y, static_cast<XT *>(P.partial));
+            P.tiles, P.chunk_off, P.slot_dst, P.slot_len, P.vrows, P.col16, P.col32,
+            static_cast<const VT *>(P.val), P.xlist, x, y, static_cast<XT *>(P.partial));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -281,14 +341,17 @@ cudaError_t launch_fixed(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
     return cudaSuccess;
 }
 
-template <int LANES, typename VT, typename XT>
+template <int R, typename VT, typename XT>
 cudaError_t launch_r(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
 {
-    switch (P.nrhs) {
-    case 1: return launch_fixed<LANES, 1, VT, XT>(P, x, y, s);
-    case 2: return launch_fixed<LANES, 2, VT, XT>(P, x, y, s);
-    case 4: return launch_fixed<LANES, 4, VT, XT>(P, x, y, s);
-    case 8: return launch_fixed<LANES, 8, VT, XT>(P, x, y, s);
+    if (!P.use_k1) return launch_tiled<R, VT, XT>(P, x, y, s);
+    switch (P.lanes) {
+    case 1: return launch_k1<1, R, VT, XT>(P, x, y, s);
+    case 2: return launch_k1<2, R, VT, XT>(P, x, y, s);
+    case 4: return launch_k1<4, R, VT, XT>(P, x, y, s);
+    case 8: return launch_k1<8, R, VT, XT>(P, x, y, s);
+    case 16: return launch_k1<16, R, VT, XT>(P, x, y, s);
+    case 32: return launch_k1<32, R, VT, XT>(P, x, y, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -299,12 +362,11 @@ cudaError_t launch_exec(const DevPlan &P, const void *xv, void *yv, cudaStream_t
     const XT *x = static_cast<const XT *>(xv);
     XT *y = static_cast<XT *>(yv);
     if (P.m == 0) return cudaSuccess;
-    switch (P.lanes) {
+    switch (P.nrhs) {
+    case 1: return launch_r<1, VT, XT>(P, x, y, s);
     case 2: return launch_r<2, VT, XT>(P, x, y, s);
     case 4: return launch_r<4, VT, XT>(P, x, y, s);
     case 8: return launch_r<8, VT, XT>(P, x, y, s);
-    case 16: return launch_r<16, VT, XT>(P, x, y, s);
-    case 32: return launch_r<32, VT, XT>(P, x, y, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -205,144 +205,233 @@ namespace {
 
 struct TileCfg {
     int32_t W;          // staging capacity (x entries)
-    int32_t tnnz;       // nonzero budget per tile
+    int32_t tnnz;       // nonzero budget of a staging tile
+    int32_t gnnz;       // nonzero budget of a tile that stages nothing
     int32_t long_t;     // rows longer than this become chunks
-    int32_t chunk;      // nonzeros per chunk
+    int32_t chunk;      // nonzeros per chunk of a long row
     int32_t max_rows;   // rows per tile
+    int32_t vrow_len;   // rows longer than this are reduced by a whole warp
     bool stage;         // staging allowed
-    double min_reuse;   // stage only if nnz >= min_reuse * gathered list entries
 };
 
+// Cuts the plan rows of one part into tiles.  A tile keeps adding rows while
+// the x entries it reuses (touched at least twice) still fit the staging
+// capacity W -- the shared-memory version of "every R_k fits into the cache"
+// (Theorem 1).  At the end each column of the tile is either staged (inside
+// the part's contiguous home range, or reused) or gathered directly from L2
+// (touched once, outside the home range), and the tile's rows are sorted by
+// length into chunks of 32 stored column-major.
 struct Tiler {
     const TileCfg cfg;
     const std::vector<int32_t> &prp;   // plan row starts
     const std::vector<int32_t> &col;   // plan-order global columns
+    const std::vector<double> &pval;   // plan-order values
+    const std::vector<int32_t> &pdst;  // plan row -> slot_dst encoding
     HostPlan &P;
-    std::vector<int32_t> mark, mark2, loc;
+    std::vector<int32_t> mark, cnt, loc;
     int32_t stamp = 0;
-    std::vector<int32_t> distinct;
+    std::vector<int32_t> used;
+    std::vector<int32_t> order;
 
     Tiler(const TileCfg &c, const std::vector<int32_t> &rp, const std::vector<int32_t> &cl,
-          HostPlan &plan, int32_t n)
-        : cfg(c), prp(rp), col(cl), P(plan), mark((size_t)n, -1), mark2((size_t)n, -1),
-          loc((size_t)n, 0) {}
+          const std::vector<double> &pv, const std::vector<int32_t> &pd, HostPlan &plan,
+          int32_t n)
+        : cfg(c), prp(rp), col(cl), pval(pv), pdst(pd), P(plan), mark((size_t)n, -1),
+          cnt((size_t)n, 0), loc((size_t)n, 0) {}
 
-    // Close a tile over plan rows [r0, r1) whose distinct columns carry mark
-    // == stamp.  Decide staged vs global, pick the contiguous run, fill local
-    // indices.  y0 as in Tile.
-    void emit(int32_t r0, int32_t r1, int32_t y0, int32_t h0, int32_t h1, bool force_global)
+    // Close the tile made of plan rows `rows`; its columns carry mark == stamp
+    // and their use counts in cnt.
+    void emit(const std::vector<int32_t> &rows, int64_t tile_nnz, int32_t h0, int32_t h1,
+              bool force_global)
     {
-        if (r1 <= r0) return;
-        const int32_t p0 = prp[r0], p1 = prp[r1];
-        const int32_t tile_nnz = p1 - p0;
+        if (rows.empty()) return;
         Tile t{};
-        t.r0 = r0;
-        t.r1 = r1;
-        t.y0 = y0;
-        bool staged = cfg.stage && !force_global && tile_nnz > 0;
-        if (staged) {
-            distinct.clear();
-            for (int32_t q = p0; q < p1; ++q) {
-                int32_t c = col[q];
-                if (mark2[c] != stamp) {
-                    mark2[c] = stamp;
-                    distinct.push_back(c);
-                }
-            }
-            std::sort(distinct.begin(), distinct.end());
-            // contiguous run inside the home column range, if dense enough
-            int32_t lo = -1, hi = -1, in_home = 0;
-            for (int32_t c : distinct)
-                if (c >= h0 && c < h1) {
+        t.kind = TILE_GLOBAL;
+        if (cfg.stage && !force_global && tile_nnz > 0) {
+            std::sort(used.begin(), used.end());
+            int32_t lo = -1, hi = -1;
+            for (int32_t c : used)
+                if (c >= h0 && c < h1 && cnt[c] >= 2) {
                     if (lo < 0) lo = c;
                     hi = c;
-                    ++in_home;
                 }
-            int32_t runlen = 0, run0 = 0;
-            if (in_home > 0) {
-                int32_t span = hi - lo + 1;
-                int32_t others = (int32_t)distinct.size() - in_home;
-                if (span <= 2 * in_home && span + others <= cfg.W) {
+            int32_t run0 = 0, runlen = 0;
+            if (lo >= 0) {
+                int32_t inspan = 0;
+                for (int32_t c : used) inspan += (c >= lo && c <= hi);
+                const int32_t span = hi - lo + 1;
+                if (span <= 2 * inspan) {
                     run0 = lo;
                     runlen = span;
                 }
             }
-            int32_t listlen = 0;
-            for (int32_t c : distinct)
-                if (!(runlen > 0 && c >= run0 && c < run0 + runlen)) ++listlen;
-            if (runlen + listlen > cfg.W ||
-                (double)tile_nnz < cfg.min_reuse * (double)listlen)
-                staged = false;
-            if (staged) {
-                t.kind = TILE_STAGED;
+            auto in_run = [&](int32_t c) { return runlen > 0 && c >= run0 && c < run0 + runlen; };
+            int32_t listlen = 0, direct = 0;
+            int64_t staged_uses = 0;
+            for (int32_t c : used) {
+                if (in_run(c)) {
+                    staged_uses += cnt[c];
+                } else if (cnt[c] >= 2) {
+                    ++listlen;
+                    staged_uses += cnt[c];
+                } else {
+                    direct += cnt[c];
+                }
+            }
+            if (runlen + listlen > cfg.W) {
+                // the run does not fit beside the reused columns: list only
+                runlen = listlen = direct = 0;
+                staged_uses = 0;
+                for (int32_t c : used) {
+                    if (cnt[c] >= 2) {
+                        ++listlen;
+                        staged_uses += cnt[c];
+                    } else {
+                        direct += cnt[c];
+                    }
+                }
+            }
+            const int32_t staged = runlen + listlen;
+            // stage only when the staged entries are reused on average
+            if (staged > 0 && staged <= cfg.W && (double)staged_uses >= 1.5 * (double)staged) {
+                t.kind = direct == 0 ? TILE_NARROW : TILE_MIXED;
                 t.run0 = run0;
                 t.runlen = runlen;
                 t.list0 = (int32_t)P.xlist.size();
                 t.listlen = listlen;
                 int32_t pos = runlen;
-                for (int32_t c : distinct) {
-                    if (runlen > 0 && c >= run0 && c < run0 + runlen) {
-                        loc[c] = c - run0;
-                    } else {
+                for (int32_t c : used) {
+                    if (in_run(c)) loc[c] = c - run0;
+                    else if (cnt[c] >= 2) {
                         loc[c] = pos++;
                         P.xlist.push_back(c);
+                    } else {
+                        loc[c] = -1;
                     }
                 }
-                for (int32_t q = p0; q < p1; ++q) P.col16[q] = (uint16_t)loc[col[q]];
-                P.staged_entries += runlen + listlen;
+                P.staged_entries += staged;
                 P.list_entries += listlen;
+                P.direct_nnz += direct;
+                if (t.kind == TILE_NARROW) P.narrow_nnz += tile_nnz;
                 P.n_staged_tiles++;
             }
         }
-        if (!staged) {
-            t.kind = TILE_GLOBAL;
+        if (t.kind == TILE_GLOBAL) {
             P.n_global_tiles++;
+            P.direct_nnz += tile_nnz;
+        }
+        // rows longer than cfg.vrow_len are reduced by a whole warp; the rest
+        // go by decreasing length (stable) into chunks of 32, column-major
+        auto put = [&](size_t e, int32_t q) {
+            const int32_t cg = col[q];
+            P.val[e] = pval[q];
+            if (t.kind == TILE_NARROW) P.col16[e] = (uint16_t)loc[cg];
+            else if (t.kind == TILE_MIXED) P.col32[e] = loc[cg] >= 0 ? loc[cg] : ~cg;
+            else P.col32[e] = cg;
+        };
+        order.clear();
+        t.vrow0 = (int32_t)P.vrows.size();
+        for (int32_t r : rows) {
+            const int32_t a = prp[r], len = prp[r + 1] - a;
+            if (len <= cfg.vrow_len) {
+                order.push_back(r);
+                continue;
+            }
+            const size_t e0 = P.val.size();
+            P.val.resize(e0 + len, 0.0);
+            P.col32.resize(e0 + len, 0);
+            P.col16.resize(e0 + len, 0);
+            for (int32_t k = 0; k < len; ++k) put(e0 + k, a + k);
+            P.vrows.push_back(VRow{(int32_t)e0, len, pdst[r], 0});
+            P.padded_elems += len;
+            P.fma_slots += ((len + 31) / 32) * 32;
+        }
+        t.nvrows = (int32_t)P.vrows.size() - t.vrow0;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return prp[a + 1] - prp[a] > prp[b + 1] - prp[b];
+        });
+        t.chunk0 = (int32_t)P.chunk_off.size();
+        const int32_t nrows = (int32_t)order.size();
+        t.nchunks = (nrows + 31) / 32;
+        for (int32_t c = 0; c < t.nchunks; ++c) {
+            const int32_t first = c * 32;
+            const int32_t L = prp[order[first] + 1] - prp[order[first]];
+            const size_t off = P.val.size();
+            P.chunk_off.push_back((int32_t)off);
+            P.val.resize(off + (size_t)L * 32, 0.0);
+            P.col32.resize(off + (size_t)L * 32, 0);
+            P.col16.resize(off + (size_t)L * 32, 0);
+            P.padded_elems += (int64_t)L * 32;
+            P.fma_slots += (int64_t)L * 32;
+            for (int32_t i = 0; i < 32; ++i) {
+                const int32_t idx = first + i;
+                if (idx >= nrows) {
+                    P.slot_dst.push_back(-1);
+                    P.slot_len.push_back(0);
+                    continue;
+                }
+                const int32_t r = order[idx];
+                const int32_t a = prp[r], len = prp[r + 1] - a;
+                P.slot_dst.push_back(pdst[r]);
+                P.slot_len.push_back(len);
+                for (int32_t k = 0; k < len; ++k) put(off + (size_t)k * 32 + i, a + k);
+            }
         }
         P.tiles.push_back(t);
     }
 
-    // Tile plan rows [rb, re).  chunked[r] marks rows handled as chunks.
-    // identity: plan row r writes y[r] (SB/DB); else via dst.
-    void tile_rows(int32_t rb, int32_t re, int32_t h0, int32_t h1, bool identity,
+    // Tile plan rows [rb, re) of one part with home columns [h0, h1).
+    // chunked[r] marks rows handled as chunks (left out of the tiles).
+    void tile_rows(int32_t rb, int32_t re, int32_t h0, int32_t h1,
                    const std::vector<char> &chunked, bool force_global)
     {
-        int32_t cur0 = -1, cur_rows = 0, cur_nnz = 0, cur_d = 0;
-        auto close = [&](int32_t end) {
-            if (cur0 >= 0) emit(cur0, end, identity ? cur0 : -1, h0, h1, force_global);
-            cur0 = -1;
-            cur_rows = cur_nnz = cur_d = 0;
+        const bool staging = cfg.stage && !force_global;
+        const int32_t limit = staging ? cfg.tnnz : cfg.gnnz;
+        int64_t cur_nnz = 0;
+        int32_t multi = 0;
+        std::vector<int32_t> rows;
+        auto close = [&]() {
+            emit(rows, cur_nnz, h0, h1, force_global);
+            rows.clear();
+            cur_nnz = multi = 0;
+            used.clear();
             ++stamp;
         };
         for (int32_t r = rb; r < re; ++r) {
-            if (chunked[r]) {
-                close(r);
-                continue;
-            }
+            if (chunked[r]) continue;
             const int32_t a = prp[r], b = prp[r + 1], len = b - a;
-            int32_t newd = 0;
-            if (cur0 >= 0)
-                for (int32_t q = a; q < b; ++q) newd += (mark[col[q]] != stamp);
-            if (cur0 >= 0 && (cur_d + newd > cfg.W || cur_nnz + len > cfg.tnnz ||
-                              cur_rows >= cfg.max_rows)) {
-                close(r);
+            if (!rows.empty()) {
+                int32_t newmulti = 0;
+                if (staging)
+                    for (int32_t q = a; q < b; ++q) {
+                        const int32_t c = col[q];
+                        newmulti += (mark[c] == stamp && cnt[c] == 1);
+                    }
+                if (multi + newmulti > cfg.W || cur_nnz + len > limit ||
+                    (int32_t)rows.size() >= cfg.max_rows)
+                    close();
             }
-            if (cur0 < 0) {
-                cur0 = r;
-                newd = len;
+            rows.push_back(r);
+            for (int32_t q = a; q < b; ++q) {
+                const int32_t c = col[q];
+                if (mark[c] != stamp) {
+                    mark[c] = stamp;
+                    cnt[c] = 1;
+                    used.push_back(c);
+                } else {
+                    if (cnt[c] == 1) ++multi;
+                    ++cnt[c];
+                }
             }
-            for (int32_t q = a; q < b; ++q) mark[col[q]] = stamp;
-            cur_d += newd;
             cur_nnz += len;
-            cur_rows++;
         }
-        close(re);
+        close();
     }
 };
 
-int32_t pow2_lanes(double mean)
+int32_t pow2_at_least(double want, int32_t lo)
 {
-    double want = mean / 2.0;
-    int32_t l = 2;
+    int32_t l = lo;
     while (l < 32 && l < want) l *= 2;
     return l;
 }
@@ -367,9 +456,9 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         set_error("nrhs=%d: supported right-hand-side counts are 1, 2, 4, 8", o.nrhs);
         return SPMV_E_UNSUPPORTED;
     }
-    if (o.lanes != 0 && o.lanes != 2 && o.lanes != 4 && o.lanes != 8 && o.lanes != 16 &&
-        o.lanes != 32) {
-        set_error("lanes=%d: must be 0, 2, 4, 8, 16 or 32", o.lanes);
+    if (o.lanes != 0 && o.lanes != 1 && o.lanes != 2 && o.lanes != 4 && o.lanes != 8 &&
+        o.lanes != 16 && o.lanes != 32) {
+        set_error("lanes=%d: must be 0, 1, 2, 4, 8, 16 or 32", o.lanes);
         return SPMV_E_INVALID;
     }
     const int32_t form = splits ? splits->form : SPMV_NATURAL;
@@ -380,10 +469,12 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     const int32_t m = A->m, n = A->n;
     const int64_t nnz = A->nnz;
     const int xb = (o.dtype == SPMV_F64) ? 8 : 4;
-    int32_t W = o.tile_cols > 0 ? o.tile_cols : (48 * 1024) / (xb * o.nrhs);
-    if ((int64_t)W * xb * o.nrhs > 227 * 1024 || W > 65535) {
+    const int r = o.nrhs;
+    // shared memory of a CTA: the staged x entries
+    int32_t W = o.tile_cols > 0 ? o.tile_cols : (48 * 1024) / (xb * r);
+    if ((int64_t)W * xb * r > 220 * 1024 || W > 65535) {
         set_error("tile_cols=%d does not fit shared memory (x entries of %d bytes, r=%d)", W,
-                  xb, o.nrhs);
+                  xb, r);
         return SPMV_E_UNSUPPORTED;
     }
     P->m = m;
@@ -391,7 +482,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     P->nnz = nnz;
     P->form = form;
     P->dtype = o.dtype;
-    P->nrhs = o.nrhs;
+    P->nrhs = r;
     P->flags = o.flags;
     P->tile_cols = W;
 
@@ -412,7 +503,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     if (form == SPMV_NATURAL && !(o.flags & SPMV_FLAG_TILED_NATURAL)) {
         P->use_k1 = true;
         P->K = 1;
-        P->lanes = o.lanes ? o.lanes : pow2_lanes(mean_len);
+        P->lanes = o.lanes ? o.lanes : pow2_at_least(mean_len / 6.0, 2);
         P->long_thresh = o.long_row > 0 ? o.long_row : std::max(1024, 64 * P->lanes);
         P->rowptr.swap(Ah.rp);
         P->col32.swap(Ah.col);
@@ -539,41 +630,37 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     P->K = K;
     const int32_t R = (int32_t)prow.size();
 
-    // tile configuration
     TileCfg cfg;
     cfg.W = W;
-    cfg.tnnz = o.tile_nnz > 0 ? o.tile_nnz : 8192;
-    cfg.long_t = std::min(o.long_row > 0 ? o.long_row : 2048, W);
-    cfg.chunk = std::max(cfg.long_t, 1024);
     cfg.max_rows = 4096;
-    cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING);
-    cfg.min_reuse = 1.25;
+    cfg.long_t = o.long_row > 0 ? o.long_row : 1024;
+    cfg.chunk = 4096;
+    cfg.vrow_len = 64;
+    // tiles sized so that a launch has several waves of CTAs: about
+    // nnz / (152 SMs * 8) nonzeros each, within [2048, 8 W]
     {
-        // mean length of the rows the row kernels see
-        int64_t s = 0, c = 0;
-        for (int32_t r = 0; r < R; ++r) {
-            int32_t len = prp[r + 1] - prp[r];
-            if (len <= cfg.long_t) {
-                s += len;
-                ++c;
-            }
-        }
-        P->lanes = o.lanes ? o.lanes : pow2_lanes(c ? (double)s / (double)c : 1.0);
+        const int64_t want = nnz / (152 * 8);
+        cfg.tnnz = o.tile_nnz > 0 ? o.tile_nnz
+                                  : (int32_t)std::min<int64_t>(std::max<int64_t>(want, 2048),
+                                                               std::max<int64_t>(8LL * W, 2048));
+        cfg.gnnz = o.tile_nnz > 0 ? o.tile_nnz : std::max<int32_t>(2048, std::min(cfg.tnnz, 8192));
     }
+    cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING);
+    P->lanes = 32;                 // one lane per row, 32 rows per chunk
     P->long_thresh = cfg.long_t;
 
     // pieces per plan row, slots and fix-ups (split rows shared by several
     // parts and chunked long rows are summed in part / chunk order)
     std::vector<char> chunked((size_t)R, 0), has_chunk((size_t)m, 0);
     std::vector<int32_t> pieces((size_t)R, 1), tot((size_t)m, 0);
-    for (int32_t r = 0; r < R; ++r) {
-        int32_t len = prp[r + 1] - prp[r];
+    for (int32_t q = 0; q < R; ++q) {
+        int32_t len = prp[q + 1] - prp[q];
         if (len > cfg.long_t) {
-            chunked[r] = 1;
-            has_chunk[prow[r]] = 1;
-            pieces[r] = (len + cfg.chunk - 1) / cfg.chunk;
+            chunked[q] = 1;
+            has_chunk[prow[q]] = 1;
+            pieces[q] = (len + cfg.chunk - 1) / cfg.chunk;
         }
-        tot[prow[r]] += pieces[r];
+        tot[prow[q]] += pieces[q];
     }
     std::vector<int32_t> base((size_t)m, -1);
     int64_t slots = 0;
@@ -583,65 +670,84 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
             P->fixups.push_back(Fixup{i, (int32_t)slots, tot[i], 0});
             slots += tot[i];
         }
-    if (slots >= INT32_MAX) {
+    if (slots >= INT32_MAX / 2) {
         set_error("too many partial sums");
         return SPMV_E_UNSUPPORTED;
     }
     P->partial_slots = slots;
-    const bool identity = (form == SPMV_SB || form == SPMV_DB || form == SPMV_NATURAL);
-    std::vector<int32_t> run((size_t)m, 0);
-    if (!identity) P->dst.assign((size_t)R, 0);
-    std::vector<Tile> chunk_tiles;
-    for (int32_t r = 0; r < R; ++r) {
-        int32_t i = prow[r];
+    std::vector<int32_t> run((size_t)m, 0), pdst((size_t)R, -1);
+    std::vector<std::pair<int32_t, int32_t>> chunk_rows;   // (plan row, first slot)
+    for (int32_t q = 0; q < R; ++q) {
+        int32_t i = prow[q];
         int32_t slot = base[i] >= 0 ? base[i] + run[i] : -1;
-        run[i] += pieces[r];
-        if (!identity) P->dst[r] = (slot >= 0) ? -(slot + 1) : i;
-        if (chunked[r]) {
-            for (int32_t c = 0; c < pieces[r]; ++c) {
-                Tile t{};
-                t.kind = TILE_CHUNK;
-                t.r0 = prp[r] + c * cfg.chunk;
-                t.r1 = std::min(prp[r + 1], t.r0 + cfg.chunk);
-                t.y0 = slot + c;
-                chunk_tiles.push_back(t);
-            }
-        }
+        run[i] += pieces[q];
+        pdst[q] = (slot >= 0) ? dst_partial(slot) : i;
+        if (chunked[q]) chunk_rows.emplace_back(q, slot);
     }
-    // chunk tiles first so the longest work starts early
-    P->tiles = chunk_tiles;
-    P->n_chunk_tiles = (int32_t)chunk_tiles.size();
-    P->col16.assign((size_t)nnz, 0);
+    std::vector<double> pval((size_t)nnz);
+    for (int64_t q = 0; q < nnz; ++q) pval[q] = A->vals[psrc[q]];
 
-    Tiler tiler(cfg, prp, pcol, *P, n);
+    Tiler tiler(cfg, prp, pcol, pval, pdst, *P, n);
     for (int32_t k = 0; k < K; ++k) {
-        int32_t h0 = 0, h1 = n;
+        int32_t h0 = 0, h1 = 0;
         if (!cp_part.empty()) {
             h0 = cp_part[k];
             h1 = cp_part[k + 1];
+        } else if (form == SPMV_NATURAL) {
+            h0 = 0;
+            h1 = n;
         }
-        tiler.tile_rows(pr_part[k], pr_part[k + 1], h0, h1, identity, chunked, false);
+        tiler.tile_rows(pr_part[k], pr_part[k + 1], h0, h1, chunked, false);
     }
     // DB row border R_B: x entries gathered through L2, as the paper charges
     // every border nonzero a miss (eq. 6)
     if (pr_part[K + 1] > pr_part[K])
-        tiler.tile_rows(pr_part[K], pr_part[K + 1], 0, 0, identity, chunked, true);
+        tiler.tile_rows(pr_part[K], pr_part[K + 1], 0, 0, chunked, true);
 
-    P->rowptr.swap(prp);
-    P->col32.swap(pcol);
-    P->val.resize((size_t)nnz);
-    for (int64_t q = 0; q < nnz; ++q) P->val[q] = A->vals[psrc[q]];
+    // long rows: contiguous, global indices, one CTA per chunk of nonzeros;
+    // chunk tiles go first so the longest work starts early
+    std::vector<Tile> chunk_tiles;
+    for (auto &cr : chunk_rows) {
+        const int32_t q = cr.first, slot = cr.second;
+        const size_t e0 = P->val.size();
+        const int32_t a = prp[q], len = prp[q + 1] - a;
+        if (e0 + (size_t)len >= (size_t)INT32_MAX) {
+            set_error("too many stored elements");
+            return SPMV_E_UNSUPPORTED;
+        }
+        for (int32_t k = 0; k < len; ++k) {
+            P->val.push_back(pval[a + k]);
+            P->col32.push_back(pcol[a + k]);
+            P->col16.push_back(0);
+        }
+        for (int32_t c = 0; c < pieces[q]; ++c) {
+            Tile t{};
+            t.kind = TILE_CHUNK;
+            t.e0 = (int32_t)e0 + c * cfg.chunk;
+            t.e1 = std::min((int32_t)(e0 + len), t.e0 + cfg.chunk);
+            t.slot = slot + c;
+            chunk_tiles.push_back(t);
+        }
+    }
+    P->n_chunk_tiles = (int32_t)chunk_tiles.size();
+    chunk_tiles.insert(chunk_tiles.end(), P->tiles.begin(), P->tiles.end());
+    P->tiles.swap(chunk_tiles);
+    if (P->val.size() >= (size_t)INT32_MAX) {
+        set_error("too many stored elements");
+        return SPMV_E_UNSUPPORTED;
+    }
+    if (P->narrow_nnz == 0) {
+        P->col16.clear();
+        P->col16.shrink_to_fit();
+    }
 
-    // coverage: every y row is written exactly once (by a tile row or a fix-up)
+    // coverage: every y row is written exactly once (by a tile slot or a fix-up)
     {
         std::vector<int32_t> cover((size_t)m, 0);
-        for (const Tile &t : P->tiles) {
-            if (t.kind == TILE_CHUNK) continue;
-            for (int32_t r = t.r0; r < t.r1; ++r) {
-                if (t.y0 >= 0) cover[t.y0 + (r - t.r0)]++;
-                else if (P->dst[r] >= 0) cover[P->dst[r]]++;
-            }
-        }
+        for (int32_t d : P->slot_dst)
+            if (d >= 0) cover[d]++;
+        for (const VRow &v : P->vrows)
+            if (v.dst >= 0) cover[v.dst]++;
         for (const Fixup &f : P->fixups) cover[f.row]++;
         for (int32_t i = 0; i < m; ++i)
             if (cover[i] != 1) {

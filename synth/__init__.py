@@ -174,28 +174,34 @@ def mesh5(nx=1024, seed=0, permute=True):
 
 
 def rmat(scale=20, deg=16, a=0.57, b=0.19, c=0.19, seed=0, chunk=1 << 22):
-    """R-MAT graph with exactly deg * 2^scale distinct directed pairs."""
+    """R-MAT graph with exactly deg * 2^scale distinct directed pairs: edges
+    are drawn in batches, and the first deg * 2^scale distinct pairs in draw
+    order are kept."""
     rng = _rng(seed)
     n = 1 << scale
     target = deg * n
-    keys = np.empty(0, dtype=np.int64)
-    ab, abc = a + b, a + b + c
+    ab, abc = np.float32(a + b), np.float32(a + b + c)
+    fa = np.float32(a)
+    batches = []
+    drawn = 0
+    want = int(target * 1.3) + chunk
     while True:
-        i = np.zeros(chunk, dtype=np.int64)
-        j = np.zeros(chunk, dtype=np.int64)
-        for _ in range(scale):
-            u = rng.random(chunk)
-            bi = (u >= ab).astype(np.int64)
-            bj = (((u >= a) & (u < ab)) | (u >= abc)).astype(np.int64)
-            i = (i << 1) | bi
-            j = (j << 1) | bj
-        keys = np.concatenate([keys, (i << scale) | j])
+        while drawn < want:
+            k = min(chunk, want - drawn)
+            i = np.zeros(k, dtype=np.int64)
+            j = np.zeros(k, dtype=np.int64)
+            for _ in range(scale):
+                u = rng.random(k, dtype=np.float32)
+                i = (i << 1) | (u >= ab)
+                j = (j << 1) | (((u >= fa) & (u < ab)) | (u >= abc))
+            batches.append((i << scale) | j)
+            drawn += k
+        keys = np.concatenate(batches)
         uniq, first = np.unique(keys, return_index=True)
         if uniq.size >= target:
-            keep = np.sort(first)[:target]
-            keys = keys[keep]
+            keys = keys[np.sort(first)[:target]]
             break
-        keys = keys[np.sort(first)]
+        want = drawn + int((target - uniq.size) * 1.5) + chunk
     rows, cols = keys >> scale, keys & (n - 1)
     vals = rng.uniform(-1.0, 1.0, size=rows.size)
     return coo_to_csr(n, n, rows, cols, vals)

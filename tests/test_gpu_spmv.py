@@ -67,7 +67,7 @@ def test_natural_zipf(zipf, dtype, nrhs):
     _check(plan, m, n, rp, ci, v, x)
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 def test_natural_lanes_exact(zipf, lanes):
     m, n, rp, ci, _ = zipf
     vi = synth.integer_values(int(rp[-1]), 5)
