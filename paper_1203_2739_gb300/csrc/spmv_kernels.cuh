@@ -37,12 +37,74 @@ namespace spmv {
 
 constexpr int kThreads = 256;
 
-// value load, streamed with evict-first so the matrix does not push x out of L2
-__device__ __forceinline__ double load_val(const double *p) { return __ldcs(p); }
-__device__ __forceinline__ float load_val(const float *p) { return __ldcs(p); }
+// Tuning knobs (compile-time):
+//   SPMV_STREAM_HINT  how the matrix stream (values, indices) is loaded:
+//                     0 = ld.global.cs (evict-first), 1 = ld.global.nc with
+//                     L1::no_allocate (keeps L1 for x), 2 = ld.global.nc
+//   SPMV_TILE_MINBLOCKS  minimum resident CTAs per SM asked of the compiler
+//                     for the tiled kernel (register budget)
+#ifndef SPMV_STREAM_HINT
+#define SPMV_STREAM_HINT 0
+#endif
+#ifndef SPMV_TILE_MINBLOCKS
+#define SPMV_TILE_MINBLOCKS 1
+#endif
+
+// loads of the matrix stream, read exactly once per SpMV
+__device__ __forceinline__ double ld_stream(const double *p)
+{
+#if SPMV_STREAM_HINT == 1
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+#elif SPMV_STREAM_HINT == 2
+    return __ldg(p);
+#else
+    return __ldcs(p);
+#endif
+}
+__device__ __forceinline__ float ld_stream(const float *p)
+{
+#if SPMV_STREAM_HINT == 1
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+#elif SPMV_STREAM_HINT == 2
+    return __ldg(p);
+#else
+    return __ldcs(p);
+#endif
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p)
+{
+#if SPMV_STREAM_HINT == 1
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#elif SPMV_STREAM_HINT == 2
+    return __ldg(p);
+#else
+    return __ldcs(p);
+#endif
+}
+__device__ __forceinline__ uint16_t ld_stream(const uint16_t *p)
+{
+#if SPMV_STREAM_HINT == 1
+    uint16_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+#elif SPMV_STREAM_HINT == 2
+    return __ldg(p);
+#else
+    return __ldcs(p);
+#endif
+}
+
+__device__ __forceinline__ double load_val(const double *p) { return ld_stream(p); }
+__device__ __forceinline__ float load_val(const float *p) { return ld_stream(p); }
 __device__ __forceinline__ float load_val(const __nv_bfloat16 *p)
 {
-    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    const uint16_t u = ld_stream(reinterpret_cast<const uint16_t *>(p));
     return __uint_as_float(static_cast<unsigned>(u) << 16);
 }
 
@@ -92,7 +154,7 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
         for (int c = 0; c < R; ++c) s[c] = XT(0);
         for (int32_t p = p0 + (int32_t)threadIdx.x; p < p1; p += kThreads) {
             const XT v = (XT)load_val(val + p);
-            const int64_t xc = (int64_t)__ldcs(col + p) * R;
+            const int64_t xc = (int64_t)ld_stream(col + p) * R;
 #pragma unroll
             for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
         }
@@ -120,7 +182,7 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
     for (int c = 0; c < R; ++c) s[c] = XT(0);
     for (int32_t p = p0 + lane; p < p1; p += LANES) {
         const XT v = (XT)load_val(val + p);
-        const int64_t xc = (int64_t)__ldcs(col + p) * R;
+        const int64_t xc = (int64_t)ld_stream(col + p) * R;
 #pragma unroll
         for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
     }
@@ -138,7 +200,7 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
 // the chunk's rows sits at chunk_off + 32 k + i, so every load is coalesced
 // and every FP64 FMA runs with the lanes of all rows still going.
 template <int R, typename VT, typename XT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, SPMV_TILE_MINBLOCKS)
 k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
         const int32_t *__restrict__ slot_dst, const int32_t *__restrict__ slot_len,
         const VRow *__restrict__ vrows, const uint16_t *__restrict__ c16,
@@ -156,7 +218,7 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
         for (int c = 0; c < R; ++c) s[c] = XT(0);
         for (int32_t e = t.e0 + (int32_t)threadIdx.x; e < t.e1; e += kThreads) {
             const XT v = (XT)load_val(val + e);
-            const int64_t xc = (int64_t)__ldcs(c32 + e) * R;
+            const int64_t xc = (int64_t)ld_stream(c32 + e) * R;
 #pragma unroll
             for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
         }
@@ -193,7 +255,7 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
         return __ldg(x + (int64_t)(~ci) * R + c);
     };
     auto colat = [&](int64_t e) -> int32_t {
-        return kind == TILE_NARROW ? (int32_t)__ldcs(c16 + e) : __ldcs(c32 + e);
+        return kind == TILE_NARROW ? (int32_t)ld_stream(c16 + e) : ld_stream(c32 + e);
     };
     auto store = [&](int32_t d, const XT (&s)[R]) {
         if (d >= 0) {

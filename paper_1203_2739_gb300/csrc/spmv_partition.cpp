@@ -166,16 +166,17 @@ struct Coarsen {
     {
         const i32 nv = G.nv;
         std::vector<i32> match((size_t)nv, -1);
-        std::vector<std::pair<u64, i32>> order;
+        std::vector<std::tuple<double, u64, i32>> order;
         order.reserve((size_t)G.nn);
         for (i32 n = 0; n < G.nn; ++n) {
             i64 sz = G.pins_of(n);
             if (sz < 2 || sz > 4 * kNetMax) continue;
-            order.emplace_back(((u64)sz << 40) | (rng() & ((1ULL << 40) - 1)), n);
+            // heaviest connectivity c(n)/(|n|-1) first, random ties
+            order.emplace_back(-(double)G.nc[n] / (double)(sz - 1), rng(), n);
         }
         std::sort(order.begin(), order.end());
         for (auto &o : order) {
-            const i32 n = o.second;
+            const i32 n = std::get<2>(o);
             i32 prev = -1;
             for (i64 q = G.xpins[n]; q < G.xpins[n + 1]; ++q) {
                 const i32 v = G.pins[q];
@@ -764,7 +765,7 @@ void bisect_core(const HG &G, double eps, u64 seed, int threads, std::vector<uin
         levels.pop_back();     // the coarse level is no longer needed
         FM fm(fine, s, mw0, mw1);
         const bool big = fine.nv > 200000;
-        fm.refine(2, big ? 1000 : std::min<i64>(2000, std::max<i64>(100, fine.nv / 50)), rng, true);
+        fm.refine(big ? 1 : 2, big ? 1000 : std::min<i64>(2000, std::max<i64>(100, fine.nv / 50)), rng, true);
     }
     side.swap(s);
 }
@@ -795,7 +796,7 @@ struct Driver {
     // column piece disappears when its pin is removed.  single_r / single_c
     // count, per original vertex, the lone row / column pieces it holds.
     std::vector<i32> single_r, single_c;
-    std::vector<i32> col_of;             // RCN/eRCN: column of each nonzero
+    std::vector<i32> seg_of;             // RCN/eRCN: vertex (row segment) of each nonzero
 
     struct Job {
         HG H;
@@ -815,7 +816,8 @@ struct Driver {
             for (i32 v : j.H.vz) nnz += v;
             cols = j.H.nn + j.single_cols;
         } else {
-            nnz = j.H.nv;
+            nnz = 0;
+            for (i32 v : j.H.vz) nnz += v;
             rows = j.single_rows;
             cols = j.single_cols;
             for (i32 n = 0; n < j.H.nn; ++n) (j.H.nk[n] == KIND_ROW ? rows : cols)++;
@@ -954,7 +956,7 @@ struct Driver {
     }
 };
 
-HG build_model(const spmv_csr *A, int method, std::vector<i32> *col_of)
+HG build_model(const spmv_csr *A, int method, i32 seg, std::vector<i32> *seg_of)
 {
     const i32 m = A->m, n = A->n;
     const i64 nnz = A->nnz;
@@ -994,37 +996,55 @@ HG build_model(const spmv_csr *A, int method, std::vector<i32> *col_of)
         for (i32 j = 0; j < n; ++j)
             if (netof[j] >= 0) H.nid[netof[j]] = j;
     } else {
-        // vertices = nonzeros, nets = rows and columns
-        H.nv = (i32)nnz;
-        H.vw.assign((size_t)nnz, 12);
-        H.vid.resize((size_t)nnz);
-        std::iota(H.vid.begin(), H.vid.end(), 0);
-        H.vz.assign((size_t)nnz, 1);
-        col_of->resize((size_t)nnz);
-        std::vector<i64> colcnt((size_t)n + 1, 0);
-        for (i64 p = 0; p < nnz; ++p) {
-            (*col_of)[p] = A->colidx[p];
-            colcnt[A->colidx[p] + 1]++;
+        // vertices = nonzeros, nets = rows and columns.  Large matrices start
+        // from segments of `seg` consecutive nonzeros of a row (a fixed first
+        // coarsening level); seg = 1 is the plain fine-grain model.
+        const i64 nseg_max = nnz;
+        seg_of->resize((size_t)nnz);
+        std::vector<i32> seg_len;
+        seg_len.reserve((size_t)std::min<i64>(nseg_max, nnz / std::max(seg, 1) + m + 1));
+        std::vector<i32> row_seg0((size_t)m + 1, 0);
+        for (i32 i = 0; i < m; ++i) {
+            row_seg0[i] = (i32)seg_len.size();
+            for (i32 p = A->rowptr[i]; p < A->rowptr[i + 1]; p += seg) {
+                const i32 len = std::min(seg, A->rowptr[i + 1] - p);
+                for (i32 q = p; q < p + len; ++q) (*seg_of)[q] = (i32)seg_len.size();
+                seg_len.push_back(len);
+            }
         }
+        row_seg0[m] = (i32)seg_len.size();
+        const i32 ns = (i32)seg_len.size();
+        H.nv = ns;
+        H.vw.resize((size_t)ns);
+        H.vid.resize((size_t)ns);
+        H.vz.resize((size_t)ns);
+        for (i32 v = 0; v < ns; ++v) {
+            H.vw[v] = 12LL * seg_len[v];
+            H.vid[v] = v;
+            H.vz[v] = seg_len[v];
+        }
+        std::vector<i64> colcnt((size_t)n + 1, 0);
+        for (i64 p = 0; p < nnz; ++p) colcnt[A->colidx[p] + 1]++;
         const bool erc = (method == SPMV_PART_ERCN);
-        // row nets with >= 2 pins
+        // row nets with >= 2 segments
         H.xpins.assign(1, 0);
         for (i32 i = 0; i < m; ++i) {
             const i32 len = A->rowptr[i + 1] - A->rowptr[i];
-            if (len < 2) continue;
-            for (i32 p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) H.pins.push_back(p);
+            if (row_seg0[i + 1] - row_seg0[i] < 2) continue;
+            for (i32 v = row_seg0[i]; v < row_seg0[i + 1]; ++v) H.pins.push_back(v);
             H.xpins.push_back((i64)H.pins.size());
             H.nc.push_back(erc ? len : 1);
             H.nt.push_back(erc ? NET_REMOVE : NET_CONN);
             H.nk.push_back(KIND_ROW);
             H.nid.push_back(i);
         }
-        // column nets with >= 2 pins (transpose)
+        // column nets with >= 2 pins (transpose; a row's columns are distinct,
+        // so a column meets each segment at most once)
         for (i32 j = 0; j < n; ++j) colcnt[j + 1] += colcnt[j];
         std::vector<i32> bycol((size_t)nnz);
         {
             std::vector<i64> pos(colcnt.begin(), colcnt.end() - 1);
-            for (i64 p = 0; p < nnz; ++p) bycol[pos[A->colidx[p]]++] = (i32)p;
+            for (i64 p = 0; p < nnz; ++p) bycol[pos[A->colidx[p]]++] = (*seg_of)[p];
         }
         for (i32 j = 0; j < n; ++j) {
             const i64 len = colcnt[j + 1] - colcnt[j];
@@ -1099,7 +1119,12 @@ extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_op
             D.eps = opts->imbalance > 0 ? opts->imbalance : 0.10;
             D.seed = opts->seed;
             D.threads = opts->threads > 0 ? opts->threads : hardware_threads();
-            HG H = build_model(A, method, &D.col_of);
+            // row-column-net models: segments of up to `seg` nonzeros of a row
+            // keep the vertex count near 4M on large matrices
+            const i32 seg = method == SPMV_PART_CN
+                                ? 1
+                                : (i32)std::min<i64>(8, std::max<i64>(1, (nnz + 3999999) / 4000000));
+            HG H = build_model(A, method, seg, &D.seg_of);
             Driver::Job root;
             if (method == SPMV_PART_CN) {
                 // columns with a single nonzero are single-pin nets
@@ -1121,27 +1146,29 @@ extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_op
                 i64 ner = 0, nec = 0, sr = 0, sc = 0;
                 std::vector<i32> colcnt((size_t)n, 0);
                 for (i64 p = 0; p < nnz; ++p) colcnt[A->colidx[p]]++;
-                for (i32 i = 0; i < m; ++i) {
-                    const i32 len = A->rowptr[i + 1] - A->rowptr[i];
-                    ner += len > 0;
-                    sr += len == 1;
-                }
                 for (i32 j = 0; j < n; ++j) {
                     nec += colcnt[j] > 0;
                     sc += colcnt[j] == 1;
                 }
+                D.cost = 0;
+                D.row_cut.assign((size_t)m, 0);
+                D.single_r.assign((size_t)H.nv, 0);
+                D.single_c.assign((size_t)H.nv, 0);
+                for (i32 i = 0; i < m; ++i) {
+                    const i32 a = A->rowptr[i], b = A->rowptr[i + 1];
+                    ner += b > a;
+                    if (b > a && D.seg_of[a] == D.seg_of[b - 1]) {
+                        D.single_r[D.seg_of[a]]++;     // the whole row is one vertex
+                        ++sr;
+                    }
+                    for (i32 p = a; p < b; ++p)
+                        if (colcnt[A->colidx[p]] == 1) D.single_c[D.seg_of[p]]++;
+                }
                 D.cost = (method == SPMV_PART_RCN) ? ner + nec : nec;
                 root.single_rows = sr;
                 root.single_cols = sc;
-                D.row_cut.assign((size_t)m, 0);
-                D.single_r.assign((size_t)nnz, 0);
-                D.single_c.assign((size_t)nnz, 0);
-                for (i32 i = 0; i < m; ++i)
-                    for (i32 p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
-                        if (A->rowptr[i + 1] - A->rowptr[i] == 1) D.single_r[p] = 1;
-                        if (colcnt[A->colidx[p]] == 1) D.single_c[p] = 1;
-                    }
             }
+            const i32 nvert = H.nv;
             root.H = std::move(H);
             D.run(std::move(root));
             // leaves -> part ids
@@ -1153,7 +1180,6 @@ extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_op
             }
             std::sort(keys.begin(), keys.end());
             std::vector<i32> vpart;
-            const i32 nvert = (method == SPMV_PART_CN) ? m : (i32)nnz;
             vpart.assign((size_t)nvert, -1);
             if (depth >= 0) {
                 K = 1 << depth;
@@ -1175,7 +1201,9 @@ extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_op
                 cost_cols = cost;
                 cost_rows = 0;
             } else if (method == SPMV_PART_RCN) {
-                labels.swap(vpart);
+                // every nonzero takes the part of its row segment
+                labels.resize((size_t)nnz);
+                for (i64 p = 0; p < nnz; ++p) labels[p] = vpart[D.seg_of[p]];
                 form = SPMV_SPLIT;
                 // rows' share: lambda(r_i) sums, computed from the labels
                 std::vector<i32> seen((size_t)K, -1);
@@ -1197,7 +1225,7 @@ extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_op
                         labels[i] = K;
                         continue;
                     }
-                    if (A->rowptr[i + 1] > A->rowptr[i]) labels[i] = vpart[A->rowptr[i]];
+                    if (A->rowptr[i + 1] > A->rowptr[i]) labels[i] = vpart[D.seg_of[A->rowptr[i]]];
                     else labels[i] = (i32)((i64)i * K / std::max<i32>(m, 1));
                 }
                 cost_cols = cost - cost_rows;

@@ -1,0 +1,159 @@
+"""Host tests of the recursive hypergraph bisection (no GPU): the partitioner's
+own cost accounting must equal the oracle's bound computed from its labels
+(eq. 4 for the column-net model, eq. 6 for the enhanced row-column-net model,
+eq. 7 for the row-column-net model), the forms it returns must obey the
+structure rules, and planted structure must be found."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1203_2739_gb300 as S
+import synth
+
+
+def _bound(res, m, n, rp, ci):
+    K = res["K"]
+    if res["form"] == S.SPMV_SB:
+        return oracle.bound_sb(m, n, rp, ci, K, res["labels"])
+    if res["form"] == S.SPMV_DB:
+        return oracle.bound_db(m, n, rp, ci, K, res["labels"])
+    bx, by = oracle.bound_split(m, n, rp, ci, K, res["labels"])
+    return bx + by
+
+
+def _check_form(res, m, n, rp, ci):
+    K = res["K"]
+    assert oracle.is_perm(res["row_perm"]) and oracle.is_perm(res["col_perm"])
+    if res["form"] in (S.SPMV_SB, S.SPMV_DB):
+        exp = oracle.form_rows(m, n, rp, ci, K, res["labels"], border=res["form"] == S.SPMV_DB)
+        bad, _ = oracle.check_structure(m, n, rp, ci, res["row_perm"], res["col_perm"], K,
+                                        res["row_part_ptr"], res["col_part_ptr"])
+        assert bad == 0
+    else:
+        exp = oracle.form_split(m, n, rp, ci, K, res["labels"])
+    for g, e in zip((res["row_perm"], res["col_perm"], res["row_part_ptr"],
+                     res["col_part_ptr"]), exp):
+        assert np.array_equal(g, e)
+
+
+METHODS = [S.SPMV_PART_CN, S.SPMV_PART_ERCN, S.SPMV_PART_RCN]
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("shape", [(150, 150), (200, 120), (90, 260)])
+def test_reported_cost_equals_bound_fixed_k(seed, method, shape):
+    m, n = shape
+    rp, ci, _ = synth.random_sparse(m, n, 0.04, seed, empty_rows=0.05)
+    res = S.spmv_partition(m, n, rp, ci, method, K=8, seed=seed)
+    assert res["K"] == 8
+    assert res["cost"] == _bound(res, m, n, rp, ci)
+    assert res["cost_cols"] + res["cost_rows"] == res["cost"]
+    _check_form(res, m, n, rp, ci)
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("rule", [S.SPMV_FIT_CSR, S.SPMV_FIT_X])
+def test_size_rule_parts_fit(method, rule):
+    """Bisection stops when a part fits (Sec. 5.1); every leaf must fit."""
+    rp, ci, _ = synth.mesh5(40, seed=1)
+    m = n = 1600
+    budget = 6000 if rule == S.SPMV_FIT_CSR else 1200
+    res = S.spmv_partition(m, n, rp, ci, method, part_bytes=budget, fit_rule=rule, seed=3)
+    assert res["cost"] == _bound(res, m, n, rp, ci)
+    _check_form(res, m, n, rp, ci)
+    K, lab = res["K"], res["labels"]
+    assert K > 1
+    rows_of = np.repeat(np.arange(m), np.diff(rp))
+    for k in range(K):
+        if method == S.SPMV_PART_CN:
+            rows = np.nonzero(lab == k)[0]
+            nz = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows]) if rows.size else \
+                np.zeros(0, dtype=np.int64)
+        else:
+            nz = np.nonzero(lab == k)[0] if method == S.SPMV_PART_RCN else \
+                np.concatenate([np.arange(rp[i], rp[i + 1]) for i in np.nonzero(lab == k)[0]]
+                               or [np.zeros(0, dtype=np.int64)])
+            rows = np.unique(rows_of[nz])
+        cols = np.unique(ci[nz]).size
+        gcsr = method == S.SPMV_PART_RCN
+        if rule == S.SPMV_FIT_X:
+            size = cols * 8 + (rows.size * 8 if gcsr else 0)
+        else:
+            size = oracle.part_bytes(rows.size, nz.size, cols, gcsr=gcsr)
+        assert oracle.fits(size, budget) or rows.size <= 1, (k, size)
+
+
+def test_planted_blocks_are_found():
+    """8 diagonal blocks plus a few off-block nonzeros, shuffled: the column-net
+    bisection must come within 25% of the planted cut (sum lambda)."""
+    nb, bs = 8, 64
+    rp, ci, v = synth.blocks(nb=nb, bs=bs, fill=0.08, border_frac=0.01, seed=2, permute=False)
+    m = n = nb * bs
+    perm = synth.random_perm(m, 5)
+    rp2, ci2, v2 = synth.symmetric_permute(m, rp, ci, v, perm)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(m)
+    planted = (perm // bs).astype(np.int32)       # block of each (new) row
+    planted_cost = oracle.bound_sb(m, n, rp2, ci2, nb, planted)
+    res = S.spmv_partition(m, n, rp2, ci2, S.SPMV_PART_CN, K=nb, seed=0)
+    assert res["cost"] <= 1.25 * planted_cost, (res["cost"], planted_cost)
+    res = S.spmv_partition(m, n, rp2, ci2, S.SPMV_PART_RCN, K=nb, seed=0)
+    bx, by = oracle.bound_split(m, n, rp2, ci2, nb,
+                                planted[np.repeat(np.arange(m), np.diff(rp2))])
+    assert res["cost"] <= 1.25 * (bx + by)
+
+
+def test_mesh_quality_against_planted_grid():
+    """A 64 x 64 mesh cut into 4 x 4 tiles of 16 x 16: CN cost within 25%."""
+    nx = 64
+    rp, ci, _ = synth.mesh5(nx, seed=0, permute=False)
+    m = n = nx * nx
+    g = np.arange(m)
+    planted = ((g // nx) // 16 * 4 + (g % nx) // 16).astype(np.int32)
+    planted_cost = oracle.bound_sb(m, n, rp, ci, 16, planted)
+    res = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_CN, K=16, seed=0)
+    assert res["cost"] <= 1.25 * planted_cost, (res["cost"], planted_cost)
+
+
+def test_deterministic_for_seed_and_thread_count():
+    rp, ci, _ = synth.random_sparse(300, 300, 0.02, 7)
+    for method in METHODS:
+        a = S.spmv_partition(300, 300, rp, ci, method, K=16, seed=11, threads=1)
+        b = S.spmv_partition(300, 300, rp, ci, method, K=16, seed=11, threads=4)
+        c = S.spmv_partition(300, 300, rp, ci, method, K=16, seed=11, threads=4)
+        assert np.array_equal(a["labels"], b["labels"]) and np.array_equal(b["labels"], c["labels"])
+
+
+def test_random_method_and_errors():
+    rp, ci, _ = synth.random_sparse(100, 100, 0.05, 1)
+    res = S.spmv_partition(100, 100, rp, ci, S.SPMV_PART_RANDOM, K=4, seed=0)
+    assert res["K"] == 4 and res["cost"] == oracle.bound_sb(100, 100, rp, ci, 4, res["labels"])
+    with pytest.raises(S.SpmvError):
+        S.spmv_partition(100, 100, rp, ci, S.SPMV_PART_CN, K=3)
+    with pytest.raises(S.SpmvError):
+        S.spmv_partition(100, 100, rp, ci, S.SPMV_PART_CN)
+    with pytest.raises(S.SpmvError):
+        S.spmv_partition(100, 100, rp, ci, 9, K=2)
+
+
+def test_degenerate_inputs():
+    # empty matrix, single row, all-empty rows
+    rp = np.zeros(11, dtype=np.int32)
+    res = S.spmv_partition(10, 10, rp, np.zeros(0, np.int32), S.SPMV_PART_CN, K=4)
+    assert res["cost"] == 0
+    for method in METHODS:
+        rp, ci, _ = synth.random_sparse(1, 30, 0.5, 3)
+        res = S.spmv_partition(1, 30, rp, ci, method, K=2)
+        assert res["cost"] == _bound(res, 1, 30, rp, ci)
+
+
+def test_row_segments_on_large_matrices():
+    """Above 4M nonzeros the row-column-net models start from row segments;
+    the accounting must stay exact."""
+    rp, ci, _ = synth.rmat(18, 17, seed=3)
+    m = n = 1 << 18
+    assert rp[-1] > 4_000_000
+    for method in (S.SPMV_PART_RCN, S.SPMV_PART_ERCN):
+        res = S.spmv_partition(m, n, rp, ci, method, K=16, seed=1)
+        assert res["cost"] == _bound(res, m, n, rp, ci)
