@@ -261,6 +261,34 @@ void spmv_partition_free(spmv_partition_out *out);
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *spmv_last_error(void);
 
+/* y = A x for a CSR matrix that is already in device memory, allocating
+ * nothing.  The paper has no counterpart: this entry point serves callers that
+ * cannot allocate device memory when they need the product (code running
+ * inside a memory pool it does not own, a plugin given only its buffers, a
+ * step that must leave the allocator untouched).  It needs no plan.
+ *
+ * rowptr_dev[m+1], colidx_dev[nnz] (int32), vals_dev[nnz], x_dev[n] and
+ * y_dev[m] (double) are caller-owned device arrays on the current device; the
+ * CSR has the layout of spmv_csr (sorted columns not required).  y is
+ * overwritten.  Rows are reduced in chunks of 4096 nonzeros; the partial sums
+ * of rows that cross a chunk boundary go to a fixed scratch array compiled
+ * into the library (2 * SPMV_NOALLOC_MAX_NNZ / 4096 doubles = 4 MiB, held on
+ * every device that loads the library until the process exits).
+ *   - nnz > SPMV_NOALLOC_MAX_NNZ is rejected with SPMV_E_UNSUPPORTED.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing the stream into a graph.
+ *   - Every call shares the one scratch array and overwrites what it uses:
+ *     calls whose kernels overlap on the GPU (different streams, threads)
+ *     race and must be serialised by the caller.
+ * Asynchronous on `stream`.  Errors: SPMV_E_INVALID (negative size, NULL),
+ * SPMV_E_UNSUPPORTED, SPMV_E_CUDA. */
+#define SPMV_NOALLOC_MAX_NNZ 1073741824LL
+spmv_status spmv_csr_exec_noalloc(int32_t m, int32_t n, int64_t nnz,
+                                  const int32_t *rowptr_dev, const int32_t *colidx_dev,
+                                  const double *vals_dev, const double *x_dev,
+                                  double *y_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

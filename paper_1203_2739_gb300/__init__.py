@@ -43,7 +43,8 @@ DTYPE_NAMES = {SPMV_F64: "f64", SPMV_F32: "f32", SPMV_BF16: "bf16"}
 EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
            "spmv_form_from_labels", "spmv_partition", "spmv_partition_free",
-           "spmv_last_error")
+           "spmv_last_error", "spmv_csr_exec_noalloc")
+SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
 class SpmvError(RuntimeError):
@@ -131,9 +132,11 @@ def _load():
     L.spmv_partition_free.argtypes = [ctypes.POINTER(spmv_partition_out)]
     L.spmv_partition_free.restype = None
     L.spmv_last_error.restype = ctypes.c_char_p
+    L.spmv_csr_exec_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                        vp, vp, vp, vp, vp, vp]
     for name in ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
                  "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
-                 "spmv_form_from_labels", "spmv_partition"):
+                 "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -310,6 +313,29 @@ def spmv_unpermute_y(plan, y_hat, y, stream=None):
     _check(lib.spmv_unpermute_y(plan.handle, ctypes.c_void_p(y_hat.data_ptr()),
                                 ctypes.c_void_p(y.data_ptr()),
                                 ctypes.c_void_p(_stream_handle(stream))))
+
+
+def spmv_csr_exec_noalloc(m, n, rowptr, colidx, vals, x, y, stream=None):
+    """y = A x for a CSR matrix held in device tensors (int32 rowptr/colidx,
+    float64 vals, x, y), through the entry point that allocates nothing: for
+    callers that cannot allocate device memory at this point.  Partial sums
+    use the library's fixed scratch array; overlapping calls race."""
+    torch = _torch()
+    for t, dt, cnt, what in ((rowptr, torch.int32, m + 1, "rowptr"),
+                             (colidx, torch.int32, None, "colidx"),
+                             (vals, torch.float64, None, "vals"),
+                             (x, torch.float64, n, "x"), (y, torch.float64, m, "y")):
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA %s tensor" % (what, dt))
+        if cnt is not None and t.numel() != cnt:
+            raise ValueError("%s has %d elements, expected %d" % (what, t.numel(), cnt))
+    nnz = colidx.numel()
+    if vals.numel() != nnz:
+        raise ValueError("vals and colidx differ in length")
+    vp = ctypes.c_void_p
+    _check(lib.spmv_csr_exec_noalloc(m, n, nnz, vp(rowptr.data_ptr()), vp(colidx.data_ptr()),
+                                     vp(vals.data_ptr()), vp(x.data_ptr()), vp(y.data_ptr()),
+                                     vp(_stream_handle(stream))))
 
 
 # ---------------------------------------------------- host preprocessing --
