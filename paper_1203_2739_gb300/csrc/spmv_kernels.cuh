@@ -47,7 +47,7 @@ constexpr int kThreads = 256;
 #define SPMV_STREAM_HINT 0
 #endif
 #ifndef SPMV_TILE_MINBLOCKS
-#define SPMV_TILE_MINBLOCKS 1
+#define SPMV_TILE_MINBLOCKS 6
 #endif
 
 // loads of the matrix stream, read exactly once per SpMV
