@@ -5,28 +5,31 @@ plan reading its own x_hat and writing its own y_hat (device-resident inputs).
 The default workload is the FP64 reordering sweep: three 1,048,576-row
 matrices (5-point 1024^2 mesh, randomly permuted; R-MAT a,b,c = .57,.19,.19
 with 16 nonzeros per row; 64 diagonal 16,384^2 blocks at 0.2% fill plus 5%
-random off-block nonzeros, shuffled), each in natural order, a random
-symmetric permutation, the 1D SB form (column-net partitioning), the 2D DB
-form (enhanced row-column-net) and splits with K = 4, 16, 64, 256
-(row-column-net).
+random off-block nonzeros, shuffled), each in natural order, after a random
+symmetric permutation, in the 1D SB form (column-net bisection, K = 1024:
+about one part per resident CTA of a launch), the 2D DB form (enhanced
+row-column-net bisection, K = 1024) and as splits with K = 4, 16, 64, 256
+(row-column-net bisection; the smaller K are levels of the same recursion
+tree).
 
 Metric: compulsory-bytes SpMV throughput, GB/s = sum over the step of
-[nnz*(8+4) + (m+1)*4 + n*8 + m*8] / time (Sec. 2.2 streaming model), with
+[nnz*(vb+4) + (m+1)*4 + n*xb + m*xb] / time (Sec. 2.2 streaming model), with
 GFLOP/s = 2 nnz / time and the roofline of the dominant kernel against the
 measured HBM copy bandwidth.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload sweep|zipf16k|precision]
+                       [--workload sweep|zipf16k|precision] [--forms a,b,...]
+                       [--dtype f64|f32|bf16]
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import hashlib
 import json
 import os
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -36,107 +39,126 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-FORMS_SWEEP = ["natural", "random", "sb", "db", "split4", "split16", "split64", "split256"]
-
-
-# ----------------------------------------------------------------- inputs --
-def make_matrices(workload):
-    if workload == "sweep":
-        return [("mesh5_1024", synth.mesh5(1024, seed=0)),
-                ("rmat20_d16", synth.rmat(20, 16, seed=0)),
-                ("blocks64_0.2pct", synth.blocks(seed=0))]
-    if workload == "zipf16k":
-        return [("zipf16k", synth.zipf_matrix(seed=0))]
-    if workload == "precision":
-        return [("laplace3d_128", synth.laplacian3d(128, seed=0))]
-    raise ValueError(workload)
-
-
-def sizes(rp, n):
-    return len(rp) - 1, n, int(rp[-1])
+FORMS_SWEEP = ["natural", "random", "sb1024", "db1024", "split4", "split16", "split64", "split256"]
+MATRICES = {
+    "sweep": [("mesh5_1024", lambda: synth.mesh5(1024, seed=0)),
+              ("rmat20_d16", lambda: synth.rmat(20, 16, seed=0)),
+              ("blocks64_0.2pct", lambda: synth.blocks(seed=0))],
+    "zipf16k": [("zipf16k", lambda: synth.zipf_matrix(seed=0))],
+    "precision": [("laplace3d_128", lambda: synth.laplacian3d(128, seed=0))],
+}
+WORKLOAD_TEXT = {
+    "sweep": "FP64 reordering sweep: mesh 1024^2 (5-pt, permuted), R-MAT 2^20 deg 16, "
+             "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random, SB K=1024, "
+             "DB K=1024, split K=4/16/64/256",
+    "zipf16k": "Zipf 16384^2 (rows P(d)~d^-1.7498 on [1,512], Zipf(1.2) columns), natural vs SB",
+    "precision": "7-pt Dirichlet Laplacian 128^3, permuted",
+}
 
 
 def compulsory_bytes(m, n, nnz, vb=8, xb=8, r=1):
     return nnz * (vb + 4) + (m + 1) * 4 + n * xb * r + m * xb * r
 
 
-# ---------------------------------------------------------------- forms --
-def build_forms(S, name, rp, ci, n, forms, seed=0, log=None):
-    """Partition (host) for every requested form; returns {form: kwargs for
-    spmv_plan_create} and partition timings."""
-    m = len(rp) - 1
-    out, ptime = {}, {}
-    for f in forms:
+def max_over_ranks(value, device):
+    """The slowest rank's time: every rank runs the same replica of the step."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(world, step_bytes, ms_per_step):
+    """GB/s of the whole job: every rank processed step_bytes per step."""
+    return world * step_bytes / (ms_per_step * 1e-3) / 1e9
+
+
+def make_matrices(workload, log=None, only=None):
+    out = []
+    for name, fn in MATRICES[workload]:
+        if only and name not in only:
+            continue
         t0 = time.perf_counter()
-        if f == "natural":
-            out[f] = {}
-        elif f == "tiled":
-            # natural order through the tiled kernel
-            out[f] = dict(flags=S.SPMV_FLAG_TILED_NATURAL)
-        elif f == "random":
-            p = synth.random_perm(m, 1000 + seed)
-            q = p if m == n else synth.random_perm(n, 2000 + seed)
-            out[f] = dict(row_perm=p, col_perm=q)
-        elif f == "sbblock":
-            # trivial SB: K contiguous row blocks (any row partition is an SB form)
-            K = 64
-            lab = (np.arange(m, dtype=np.int64) * K // m).astype(np.int32)
-            rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SB, K, lab)
-            out[f] = dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SB, K=K,
-                          row_part_ptr=rpp, col_part_ptr=cpp)
-        elif f == "splitblock":
-            # trivial split: a 4 x 4 grid of row/column blocks
-            q = 4
-            rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp))
-            lab = ((rows * q // m) * q + (ci.astype(np.int64) * q // n)).astype(np.int32)
-            rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SPLIT, q * q,
-                                                             lab)
-            out[f] = dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SPLIT, K=q * q,
-                          row_part_ptr=rpp, col_part_ptr=cpp, nz_part=lab)
-        elif f[:2] in ("sb", "db") and f not in ("sbblock",):
-            method = S.SPMV_PART_CN if f.startswith("sb") else S.SPMV_PART_ERCN
-            if len(f) > 2:      # fixed K: bisect to depth log2(K)
-                res = S.spmv_partition(m, n, rp, ci, method, K=int(f[2:]), seed=seed)
-            else:               # size rule: bisect until the x subvector fits
-                res = S.spmv_partition(m, n, rp, ci, method, part_bytes=_part_bytes(f),
-                                       fit_rule=S.SPMV_FIT_X, seed=seed)
-            out[f] = dict(row_perm=res["row_perm"], col_perm=res["col_perm"], form=res["form"],
-                          K=res["K"], row_part_ptr=res["row_part_ptr"],
-                          col_part_ptr=res["col_part_ptr"])
-            out[f]["_cost"] = res["cost"]
-        elif f.startswith("split"):
-            K = int(f[5:])
-            res = _split_cache(S, rp, ci, m, n, K, seed)
-            out[f] = dict(row_perm=res["row_perm"], col_perm=res["col_perm"],
-                          form=S.SPMV_SPLIT, K=K, row_part_ptr=res["row_part_ptr"],
-                          col_part_ptr=res["col_part_ptr"], nz_part=res["labels"])
-            out[f]["_cost"] = res["cost"]
-        ptime[f] = time.perf_counter() - t0
+        rp, ci, v = fn()
+        out.append((name, rp, ci, v))
         if log:
-            log("  %s/%s: partition %.1fs" % (name, f, ptime[f]))
-    return out, ptime
+            log("generated %s: m=%d nnz=%d (%.1fs)" % (name, len(rp) - 1, int(rp[-1]),
+                                                        time.perf_counter() - t0))
+    return out
 
 
-_SPLIT_TREE = {}
+# ---------------------------------------------------------------- forms --
+def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
+    """Host partitions every requested form needs, run concurrently.  With
+    cache_dir, results are kept there as .npz files keyed by matrix, model,
+    K and seed, and reused (preprocessing is not part of the timed step)."""
+    m = n = len(rp) - 1
+    need = {}
+    for f in forms:
+        if f.startswith("sb"):
+            need[("cn", int(f[2:]))] = (S.SPMV_PART_CN, int(f[2:]))
+        elif f.startswith("db"):
+            need[("ercn", int(f[2:]))] = (S.SPMV_PART_ERCN, int(f[2:]))
+        elif f.startswith("split"):
+            need[("rcn", 256)] = (S.SPMV_PART_RCN, 256)
+    res = {}
+
+    def path(key):
+        return os.path.join(cache_dir, "%s_%s_K%d_s%d.npz" % (name, key[0], key[1], seed))
+
+    if cache_dir:
+        for key in list(need):
+            if os.path.exists(path(key)):
+                with np.load(path(key)) as z:
+                    res[key] = {k: (z[k] if z[k].ndim else z[k].item()) for k in z.files}
+                del need[key]
+    if not need:
+        return res
+    with cf.ThreadPoolExecutor(max_workers=len(need)) as ex:
+        futs = {key: ex.submit(S.spmv_partition, m, n, rp, ci, meth, K=K, seed=seed,
+                               threads=threads)
+                for key, (meth, K) in need.items()}
+        for key, fu in futs.items():
+            res[key] = fu.result()
+            if cache_dir:
+                os.makedirs(cache_dir, exist_ok=True)
+                np.savez(path(key), **res[key])
+    return res
 
 
-def _split_cache(S, rp, ci, m, n, K, seed):
-    """Row-column-net bisection to depth log2(256) once; K-way splits for
-    smaller K are the levels of the same recursion tree (labels >> shift)."""
-    key = (id(rp), seed)
-    if key not in _SPLIT_TREE:
-        _SPLIT_TREE[key] = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_RCN, K=256, seed=seed)
-    full = _SPLIT_TREE[key]
-    shift = int(np.log2(256 // K))
-    lab = (full["labels"] >> shift).astype(np.int32)
-    rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SPLIT, K, lab)
-    return dict(labels=lab, row_perm=rperm, col_perm=cperm, row_part_ptr=rpp,
-                col_part_ptr=cpp, cost=None)
-
-
-def _part_bytes(form):
-    # x-subvector budget per part: the default staging capacity of one tile
-    return 48 * 1024
+def form_kwargs(S, f, rp, ci, parts, seed=0):
+    """spmv_plan_create arguments of a form, and the partition it came from."""
+    m = n = len(rp) - 1
+    if f == "natural":
+        return {}, None
+    if f == "tiled":
+        return dict(flags=S.SPMV_FLAG_TILED_NATURAL), None
+    if f == "random":
+        p = synth.random_perm(m, 1000 + seed)
+        return dict(row_perm=p, col_perm=p), None
+    if f.startswith("sb") or f.startswith("db"):
+        r = parts[("cn" if f.startswith("sb") else "ercn", int(f[2:]))]
+        return dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"], K=r["K"],
+                    row_part_ptr=r["row_part_ptr"], col_part_ptr=r["col_part_ptr"]), r
+    if f.startswith("split"):
+        # A^k = the nonzeros whose K=256 label lies in the k-th of K equal
+        # label ranges (the K-way cut of the same recursion tree).  Rows and
+        # columns are grouped by the first K=256 part touching them, so the
+        # rows of each A^k keep the locality of the finer parts; the home
+        # ranges of A^k are the unions of those of its finer parts.
+        K = int(f[5:])
+        full = parts[("rcn", 256)]
+        if "fine_form" not in full:
+            full["fine_form"] = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SPLIT, 256,
+                                                        full["labels"])
+        rperm, cperm, rpp, cpp = full["fine_form"]
+        step = 256 // K
+        lab = (full["labels"] // step).astype(np.int32)
+        sel = np.r_[np.arange(0, 257, step), 257]
+        return dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SPLIT, K=K,
+                    row_part_ptr=np.ascontiguousarray(rpp[sel]),
+                    col_part_ptr=np.ascontiguousarray(cpp[sel]), nz_part=lab), full
+    raise ValueError(f)
 
 
 # ------------------------------------------------------------------ clocks --
@@ -224,39 +246,38 @@ def ncu_traffic(label):
 
 # ------------------------------------------------------------- reference --
 def run_reference(args, rank, world):
-    """The oracle timed on the host cores, on a bounded sample per step."""
+    """The CPU oracle (single-threaded FP64 compensated SpMV) timed on the
+    host, one whole-matrix SpMV per step, cycling through the matrices."""
     if rank != 0:
         return
     import oracle
-    mats = make_matrices(args.workload)
-    # one oracle SpMV of one matrix per step, cycling through the matrices
-    prepared = []
-    for name, (rp, ci, v) in mats:
-        n = len(rp) - 1          # every workload matrix is square
-        prepared.append((name, rp.astype(np.int64), ci, v, synth.uniform_x(n, 0), n))
+    mats = make_matrices(args.workload, None, args.matrices.split(",") if args.matrices else None)
+    prepared = [(name, rp.astype(np.int64), ci, v, synth.uniform_x(len(rp) - 1, 1))
+                for name, rp, ci, v in mats]
     for w in range(args.warmup):
-        name, rp, ci, v, xx, n = prepared[w % len(prepared)]
-        oracle.spmv(len(rp) - 1, n, rp, ci, v, xx)
+        name, rp, ci, v, x = prepared[w % len(prepared)]
+        oracle.spmv(len(rp) - 1, len(rp) - 1, rp, ci, v, x)
     tot_bytes, tot_flops, t = 0, 0, 0.0
     for s in range(args.steps):
-        name, rp, ci, v, xx, n = prepared[s % len(prepared)]
+        name, rp, ci, v, x = prepared[s % len(prepared)]
         m = len(rp) - 1
         t0 = time.perf_counter()
-        oracle.spmv(m, n, rp, ci, v, xx)
+        oracle.spmv(m, m, rp, ci, v, x)
         t += time.perf_counter() - t0
-        tot_bytes += compulsory_bytes(m, n, int(rp[-1]))
+        tot_bytes += compulsory_bytes(m, m, int(rp[-1]))
         tot_flops += 2 * int(rp[-1])
     gbs = tot_bytes / t / 1e9
+    sample = ("%d FP64 oracle SpMVs (compensated sums, 1 thread), one whole matrix per step "
+              "cycling %s" % (args.steps, "/".join(p[0] for p in prepared)))
     line = {
-        "impl": "reference", "metric": "SpMV GB/s (compulsory bytes)", "value": round(gbs, 3),
-        "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1e3 * t / max(args.steps, 1), 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload,
-                   "sample": "one FP64 oracle SpMV (compensated sums, 1 thread) of one sweep "
-                             "matrix per step, cycling mesh/R-MAT/blocks"},
+        "impl": "reference", "metric": "SpMV GB/s (compulsory bytes; % of GB300 HBM roofline)",
+        "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * t / max(args.steps, 1), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload]},
         "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d oracle SpMVs over the workload's matrices" % args.steps},
+                         "sample": sample},
         "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "gflops": round(tot_flops / t / 1e9, 3),
@@ -264,62 +285,67 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(mats, budget_s=15.0):
-    """Oracle SpMV on the host on a bounded sample (whole matrices, cycling)."""
+def cpu_baseline_sample(mats, budget_s):
+    """The oracle on the host on a bounded sample: whole-matrix SpMVs, cycling
+    through the workload's matrices until about budget_s seconds."""
     import oracle
-    t_tot, b_tot, count = 0.0, 0, 0
-    names = []
-    while t_tot < budget_s and count < 3 * len(mats):
-        name, (rp, ci, v), n = mats[count % len(mats)]
+    t_tot, b_tot, count, names = 0.0, 0, 0, []
+    while count < 3 * len(mats) and (t_tot < budget_s or count < len(mats)):
+        name, rp, ci, v = mats[count % len(mats)]
         m = len(rp) - 1
-        x = synth.uniform_x(n, 0)
+        x = synth.uniform_x(m, 1)
         rp64 = rp.astype(np.int64)
         t0 = time.perf_counter()
-        oracle.spmv(m, n, rp64, ci, v, x)
+        oracle.spmv(m, m, rp64, ci, v, x)
         t_tot += time.perf_counter() - t0
-        b_tot += compulsory_bytes(m, n, int(rp[-1]))
+        b_tot += compulsory_bytes(m, m, int(rp[-1]))
         count += 1
         names.append(name)
     return {"value": round(b_tot / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "%d FP64 oracle SpMVs (natural order, compensated sums): %s"
+            "sample": "%d FP64 oracle SpMVs (compensated sums, 1 thread): %s"
                       % (count, ",".join(names))}
 
 
 # ------------------------------------------------------------------- ours --
 def run_ours(args, rank, world, local_rank):
     import torch
-    import paper_1203_2739_gb300 as S
-    from tests._util import err_ratio   # test helper only measures the error
     import oracle
+    import paper_1203_2739_gb300 as S
+    from tests._util import err_ratio
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     log = (lambda s: print(s, file=sys.stderr, flush=True)) if rank == 0 else (lambda s: None)
     forms = args.forms.split(",") if args.forms else (
-        FORMS_SWEEP if args.workload == "sweep" else ["natural", "sb"])
-    t_setup = time.perf_counter()
-    mats = []
-    for name, (rp, ci, v) in make_matrices(args.workload):
-        n = len(rp) - 1
-        mats.append((name, (rp, ci, v), n))
-        log("generated %s: m=%d nnz=%d" % (name, n, int(rp[-1])))
-
+        FORMS_SWEEP if args.workload == "sweep" else ["natural", "sb8", "split16"])
     dtype = {"f64": S.SPMV_F64, "f32": S.SPMV_F32, "bf16": S.SPMV_BF16}[args.dtype]
-    entries = []   # (label, plan, x_hat, y_hat, bytes, flops, err)
+    vb, xb = {0: (8, 8), 1: (4, 4), 2: (2, 4)}[dtype]
+    tdt = torch.float64 if dtype == S.SPMV_F64 else torch.float32
+    threads = max(1, (os.cpu_count() or 4) // 2)
+    t_setup = time.perf_counter()
+    mats = make_matrices(args.workload, log, args.matrices.split(",") if args.matrices else None)
+
+    entries = []
     stream = torch.cuda.current_stream()
-    part_times = {}
-    for name, (rp, ci, v), n in mats:
-        m = len(rp) - 1
-        fk, pt = build_forms(S, name, rp, ci, n, forms, log=log)
+    for name, rp, ci, v in mats:
+        m = n = len(rp) - 1
+        t0 = time.perf_counter()
+        parts = partition_jobs(S, rp, ci, forms, seed=0, threads=threads,
+                               cache_dir=args.partition_cache, name=name)
+        log("  %s: partitions %.1fs" % (name, time.perf_counter() - t0))
+        for key, r in parts.items():
+            log("  %s %s K=%d: partition %.1fs, cost %d (cols %d, rows %d)" % (
+                name, key[0], r["K"], r["seconds"], r["cost"], r["cost_cols"], r["cost_rows"]))
         x = synth.uniform_x(n, 1)
         y_ref, absax = oracle.spmv(m, n, rp, ci, v, x)
+        xt = torch.from_numpy(x).to(dev, dtype=tdt)
         for f in forms:
-            kw = {k: val for k, val in fk[f].items() if not k.startswith("_")}
+            kw, pres = form_kwargs(S, f, rp, ci, parts)
+            t1 = time.perf_counter()
             plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, **kw)
-            xt = torch.from_numpy(x).to(dev, dtype=torch.float64 if dtype == 0 else torch.float32)
             xh = torch.empty_like(xt)
             S.spmv_permute_x(plan, xt, xh)
-            yh = torch.empty(m, dtype=xt.dtype, device=dev)
+            yh = torch.empty(m, dtype=tdt, device=dev)
             S.spmv_exec(plan, xh, yh)
             y = torch.empty_like(yh)
             S.spmv_unpermute_y(plan, yh, y)
@@ -327,13 +353,12 @@ def run_ours(args, rank, world, local_rank):
             err = err_ratio(y.double().cpu().numpy(), y_ref, absax)
             info = plan.info
             entries.append(dict(label="%s/%s" % (name, f), plan=plan, xh=xh, yh=yh,
-                                bytes=compulsory_bytes(m, n, int(rp[-1]),
-                                                       vb={0: 8, 1: 4, 2: 2}[dtype],
-                                                       xb=8 if dtype == 0 else 4),
+                                bytes=compulsory_bytes(m, n, int(rp[-1]), vb, xb),
                                 flops=2 * int(rp[-1]), err=err, info=info,
-                                cost=fk[f].get("_cost"), ptime=pt[f]))
-            log("  plan %s/%s: K=%d tiles=%d staged=%d lanes=%d err=%.2e" % (
-                name, f, info["K"], info["n_tiles"], info["n_staged_tiles"], info["lanes"], err))
+                                cost=None if pres is None else int(pres["cost"])))
+            log("  plan %s/%s: K=%d tiles=%d staged=%d err=%.2e (%.1fs)" % (
+                name, f, info["K"], info["n_tiles"], info["n_staged_tiles"], err,
+                time.perf_counter() - t1))
         del y_ref, absax
     setup_s = time.perf_counter() - t_setup
 
@@ -356,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
     clocks.start()
-    time.sleep(0.3)
+    time.sleep(0.25)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -364,13 +389,13 @@ def run_ours(args, rank, world, local_rank):
         step(ev[s])
     t1.record(stream)
     torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed_ms = t0.elapsed_time(t1)
     if dist:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-        torch.distributed.barrier()
+        elapsed_ms = max_over_ranks(elapsed_ms, dev)
     per = np.array([[a.elapsed_time(b) for (a, b) in row] for row in ev])   # steps x entries
     mean_ms = per.mean(axis=0)
 
@@ -381,7 +406,6 @@ def run_ours(args, rank, world, local_rank):
         hy = [torch.empty(e["yh"].numel(), dtype=e["yh"].dtype).pin_memory() for e in entries]
         for i, e in enumerate(entries):
             S.spmv_exec_host(e["plan"], hx[i], hy[i])
-        torch.cuda.synchronize()
         e2e_steps = max(1, min(args.steps, 5))
         ta = time.perf_counter()
         for _ in range(e2e_steps):
@@ -389,14 +413,15 @@ def run_ours(args, rank, world, local_rank):
                 S.spmv_exec_host(e["plan"], hx[i], hy[i])
         tb = time.perf_counter()
         step_bytes = sum(e["bytes"] for e in entries)
-        e2e = {"value": round(step_bytes * e2e_steps / (tb - ta) / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round(world * step_bytes * e2e_steps / (tb - ta) / 1e9, 2),
+               "unit": "GB/s",
                "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hx)),
                "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hy))}
 
     step_bytes = sum(e["bytes"] for e in entries)
     step_flops = sum(e["flops"] for e in entries)
     ms_per_step = elapsed_ms / args.steps
-    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_gbs(world, step_bytes, ms_per_step)
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
@@ -413,11 +438,10 @@ def run_ours(args, rank, world, local_rank):
             "tiles": e["info"]["n_tiles"], "staged_tiles": e["info"]["n_staged_tiles"],
             "launches": e["info"]["launches_per_exec"],
             "moved_over_compulsory": round(e["info"]["moved_bytes"] / e["bytes"], 3),
-            "partition_s": round(e["ptime"], 2), "cost": e["cost"]}
-    # natural FP64 CSR vs the best form, per matrix
+            "bound_cost": e["cost"]}
     best = {}
-    for e_label, dd in detail.items():
-        mat, form = e_label.split("/")
+    for label, dd in detail.items():
+        mat, form = label.split("/")
         if mat not in best or dd["us"] < best[mat][1]:
             best[mat] = (form, dd["us"])
     speedup = {mat: {"best_form": best[mat][0],
@@ -428,7 +452,8 @@ def run_ours(args, rank, world, local_rank):
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": args.workload, "matrices": [m[0] for m in mats], "forms": forms,
+        "config": {"workload": WORKLOAD_TEXT[args.workload],
+                   "matrices": [m[0] for m in mats], "forms": forms,
                    "unit_of_work": "one y<-Ax per (matrix, form) per step",
                    "l2": "inputs larger than L2: each step streams %.2f GB over %d plans"
                          % (step_bytes / 1e9, len(entries)),
@@ -456,22 +481,25 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "zipf16k", "precision"])
+    ap.add_argument("--workload", default="sweep", choices=sorted(MATRICES))
     ap.add_argument("--forms", default="")
+    ap.add_argument("--matrices", default="", help="subset of the workload's matrices (by name)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--partition-cache", default=None,
+                    help="directory to keep and reuse host partitions (untimed preprocessing)")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
-        print("note: warmup raised to 3", file=sys.stderr)
-        args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.warmup < 3:
+        print("note: warmup raised to 3", file=sys.stderr)
+        args.warmup = 3
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

@@ -68,8 +68,16 @@ enum { SPMV_NATURAL = 0, SPMV_SB = 1, SPMV_DB = 2, SPMV_SPLIT = 3 };
 /* plan flags */
 enum {
     SPMV_FLAG_NO_STAGING = 1,    /* never stage x in shared memory (ablation) */
-    SPMV_FLAG_TILED_NATURAL = 2  /* natural form through the tiled kernel
+    SPMV_FLAG_TILED_NATURAL = 2, /* natural form through the tiled kernel
                                     instead of the plain vector-per-row kernel */
+    SPMV_FLAG_SM_AFFINE = 4,     /* persistent CTAs that first work the tiles
+                                    queued for their own SM (a part's tiles on
+                                    one SM, sharing its L1) (ablation) */
+    SPMV_FLAG_PERSISTENT = 8     /* persistent CTAs, one per resident slot,
+                                    claiming tiles in order (ablation); the
+                                    default is one CTA per tile, with tiles
+                                    sized so that they fill about one wave of
+                                    resident CTAs */
 };
 
 /* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,
@@ -165,8 +173,17 @@ spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm,
 /* y_hat <- A_hat x_hat (Sec. 3), or y_hat <- 0; y_hat <- y_hat + A^k x_hat for
  * k = 1..K (Sec. 4), on `stream`.  x_hat: n*r device elements, y_hat: m*r
  * device elements (double for F64, float for F32/BF16), row major, no
- * aliasing.  y_hat is overwritten.  Asynchronous. */
+ * aliasing; x_hat 16-byte aligned (SPMV_E_INVALID otherwise: tiles copy
+ * their x segments with bulk copies that need it).  y_hat is overwritten.
+ * Asynchronous. */
 spmv_status spmv_exec(spmv_plan *plan, const void *x_hat, void *y_hat, void *stream);
+
+/* Synchronise `stream` and report whether any earlier spmv_exec of the plan
+ * hit a bounded device wait that gave up (the bulk copy of a tile's x
+ * segment into shared memory not completing): SPMV_E_TIMEOUT, after which
+ * the plan's results are not to be trusted and the plan should be destroyed;
+ * SPMV_OK otherwise.  spmv_exec_host checks on its own. */
+spmv_status spmv_plan_check(spmv_plan *plan, void *stream);
 
 /* spmv_exec with HOST x_hat / y_hat: copies x_hat in, runs, copies y_hat out
  * and synchronises the stream before returning.  Device staging buffers are
@@ -185,6 +202,18 @@ spmv_status spmv_plan_get_info(const spmv_plan *plan, spmv_plan_info *info);
 /* Release the plan and its device memory (synchronises the device first).
  * NULL is accepted. */
 spmv_status spmv_plan_destroy(spmv_plan *plan);
+
+/* Autotuner (not in the paper; the shapes the paper leaves to OSKI are picked
+ * by measurement here): build one plan per candidate option set for the same
+ * A / perm / splits, time `reps` calls of each on `stream` after one warm
+ * call (zero input vectors, allocated from the first candidate's allocator
+ * and released before returning), keep the fastest and destroy the others.
+ * *best receives the index of the kept candidate, *best_ms its mean time per
+ * call.  Synchronous.  Errors as spmv_plan_create, plus SPMV_E_CUDA. */
+spmv_status spmv_plan_autotune(const spmv_csr *A, const spmv_perm *perm,
+                               const spmv_splits *splits, const spmv_opts *candidates,
+                               int32_t n_candidates, int32_t reps, void *stream,
+                               spmv_plan **out, int32_t *best, float *best_ms);
 
 /* Derive a form from labels, on the host.
  *   SPMV_SB: labels[m] in [0, K): rows ordered by (label, index); C_k = the

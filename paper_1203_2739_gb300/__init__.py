@@ -13,6 +13,7 @@ Function names follow the C ABI:
     spmv_plan_create      validate, permute, split, tile, upload
     spmv_exec             y_hat <- A_hat x_hat (device tensors)
     spmv_exec_host        the same with host buffers (copies inside)
+    spmv_plan_check       report a device wait that gave up (SPMV_E_TIMEOUT)
     spmv_permute_x / spmv_unpermute_y
     spmv_plan_get_info / spmv_plan_destroy / spmv_last_error
 """
@@ -30,7 +31,8 @@ SPMV_OK, SPMV_E_INVALID, SPMV_E_STRUCTURE, SPMV_E_NOMEM, SPMV_E_CUDA, SPMV_E_TIM
     SPMV_E_UNSUPPORTED, SPMV_E_INTERNAL = range(8)
 SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
 SPMV_NATURAL, SPMV_SB, SPMV_DB, SPMV_SPLIT = 0, 1, 2, 3
-SPMV_FLAG_NO_STAGING, SPMV_FLAG_TILED_NATURAL = 1, 2
+SPMV_FLAG_NO_STAGING, SPMV_FLAG_TILED_NATURAL, SPMV_FLAG_SM_AFFINE = 1, 2, 4
+SPMV_FLAG_PERSISTENT = 8
 SPMV_PART_CN, SPMV_PART_ERCN, SPMV_PART_RCN, SPMV_PART_RANDOM = 0, 1, 2, 3
 SPMV_FIT_CSR, SPMV_FIT_X = 0, 1
 
@@ -43,7 +45,8 @@ DTYPE_NAMES = {SPMV_F64: "f64", SPMV_F32: "f32", SPMV_BF16: "bf16"}
 EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
            "spmv_form_from_labels", "spmv_partition", "spmv_partition_free",
-           "spmv_last_error", "spmv_csr_exec_noalloc")
+           "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
+           "spmv_plan_check")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
@@ -121,6 +124,7 @@ def _load():
                                    ctypes.POINTER(vp)]
     L.spmv_exec.argtypes = [vp, vp, vp, vp]
     L.spmv_exec_host.argtypes = [vp, vp, vp, vp]
+    L.spmv_plan_check.argtypes = [vp, vp]
     L.spmv_permute_x.argtypes = [vp, vp, vp, vp]
     L.spmv_unpermute_y.argtypes = [vp, vp, vp, vp]
     L.spmv_plan_get_info.argtypes = [vp, ctypes.POINTER(spmv_plan_info)]
@@ -134,9 +138,15 @@ def _load():
     L.spmv_last_error.restype = ctypes.c_char_p
     L.spmv_csr_exec_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                         vp, vp, vp, vp, vp, vp]
+    L.spmv_plan_autotune.argtypes = [ctypes.POINTER(spmv_csr), ctypes.POINTER(spmv_perm),
+                                     ctypes.POINTER(spmv_splits), ctypes.POINTER(spmv_opts),
+                                     ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp),
+                                     ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_float)]
     for name in ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
                  "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
-                 "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc"):
+                 "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
+                 "spmv_plan_autotune", "spmv_plan_check"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -247,6 +257,38 @@ def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
     return plan
 
 
+def spmv_plan_autotune(m, n, rowptr, colidx, vals, candidates, reps=5, stream=None,
+                       row_perm=None, col_perm=None, form=SPMV_NATURAL, K=0,
+                       row_part_ptr=None, col_part_ptr=None, nz_part=None,
+                       allocator="torch"):
+    """Build one plan per candidate (dicts of spmv_opts fields), time each on
+    the GPU and keep the fastest.  Returns (plan, index, ms per call)."""
+    A, keep = _csr_struct(m, n, rowptr, colidx, vals)
+    rperm = None if row_perm is None else _i32(row_perm)
+    cperm = None if col_perm is None else _i32(col_perm)
+    perm = spmv_perm(_ptr(rperm), _ptr(cperm))
+    rpp = None if row_part_ptr is None else _i32(row_part_ptr)
+    cpp = None if col_part_ptr is None else _i32(col_part_ptr)
+    nzp = None if nz_part is None else _i32(nz_part)
+    splits = spmv_splits(form, K, _ptr(rpp), _ptr(cpp), _ptr(nzp))
+    arr = (spmv_opts * len(candidates))()
+    for i, c in enumerate(candidates):
+        o = arr[i]
+        for k in ("dtype", "nrhs", "tile_cols", "tile_nnz", "long_row", "lanes", "flags"):
+            setattr(o, k, int(c.get(k, 0)))
+        if allocator == "torch":
+            o.alloc, o.release = _ALLOC_CB, _FREE_CB
+    handle = ctypes.c_void_p()
+    best = ctypes.c_int32(-1)
+    ms = ctypes.c_float(0.0)
+    _check(lib.spmv_plan_autotune(ctypes.byref(A), ctypes.byref(perm), ctypes.byref(splits), arr,
+                                  len(candidates), reps, ctypes.c_void_p(_stream_handle(stream)),
+                                  ctypes.byref(handle), ctypes.byref(best), ctypes.byref(ms)))
+    plan = Plan(handle, None)
+    plan.info = spmv_plan_get_info(plan)
+    return plan, best.value, ms.value
+
+
 def spmv_plan_get_info(plan):
     info = spmv_plan_info()
     _check(lib.spmv_plan_get_info(plan.handle, ctypes.byref(info)))
@@ -276,6 +318,12 @@ def spmv_exec(plan, x_hat, y_hat, stream=None):
     _check_vec(plan, y_hat, plan.info["m"], "y_hat")
     _check(lib.spmv_exec(plan.handle, ctypes.c_void_p(x_hat.data_ptr()),
                          ctypes.c_void_p(y_hat.data_ptr()), ctypes.c_void_p(_stream_handle(stream))))
+
+
+def spmv_plan_check(plan, stream=None):
+    """Synchronise `stream` and raise SpmvError (SPMV_E_TIMEOUT) if a bounded
+    device wait of an earlier spmv_exec of the plan gave up."""
+    _check(lib.spmv_plan_check(plan.handle, ctypes.c_void_p(_stream_handle(stream))))
 
 
 def _host_ptr(a, rows, plan, what):

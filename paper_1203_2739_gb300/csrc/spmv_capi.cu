@@ -1,6 +1,7 @@
 // C ABI entry points (include/spmv.h): plan life cycle, execution, vector
 // permutation.  Host arrays are built by spmv_plan.cpp; this file owns the
 // device memory and the launches.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -22,6 +23,7 @@ struct spmv_plan {
     const int32_t *d_row_perm = nullptr;
     const int32_t *d_col_perm = nullptr;
     void *io_x = nullptr, *io_y = nullptr;
+    int32_t *h_status = nullptr;  // pinned copy of the device status word
     size_t xbytes = 0, ybytes = 0;
 };
 
@@ -58,12 +60,13 @@ struct Arena {
         const void *host;
         size_t bytes;
         void **slot;
+        bool zero;
     };
     std::vector<Item> items;
     size_t total = 0;
-    void add(const void *host, size_t bytes, void **slot)
+    void add(const void *host, size_t bytes, void **slot, bool zero = false)
     {
-        items.push_back({host, bytes, slot});
+        items.push_back({host, bytes, slot, zero});
         total += (bytes + 255) & ~size_t(255);
     }
 };
@@ -110,7 +113,13 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
     spmv_plan *p = nullptr;
     try {
         p = new spmv_plan();
-        spmv_status st = build_host_plan(A, perm, splits, opts, &p->hp);
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            nsm = 0;        // the plan falls back to GB300's 152 SMs
+        }
+        spmv_status st = build_host_plan(A, perm, splits, opts, nsm, &p->hp);
         if (st != SPMV_OK) {
             delete p;
             return st;
@@ -157,6 +166,58 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
 
         const bool tiled = !hp.use_k1;
         const bool any_staged = tiled && hp.n_staged_tiles > 0;
+
+        // SM-affine schedule: cut the tile sequence (tiles of a part are
+        // consecutive) into one queue per SM with about equal nonzeros; the
+        // long-row chunk tiles are dealt round-robin over the queues, first
+        std::vector<int32_t> qbeg;
+        int32_t nq = 0;
+        if (tiled && (hp.flags & SPMV_FLAG_SM_AFFINE) && !hp.tiles.empty()) {
+            int nsm = 0;
+            e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+            if (e != cudaSuccess) {
+                delete p;
+                return cuda_fail(e, "cudaDeviceGetAttribute");
+            }
+            nq = std::max(1, nsm);
+            auto weight = [&](const Tile &t) -> int64_t {
+                if (t.kind == TILE_CHUNK) return t.e1 - t.e0;
+                int64_t w = 0;
+                for (int32_t v = t.vrow0; v < t.vrow0 + t.nvrows; ++v) w += hp.vrows[v].len;
+                for (int32_t ch = t.chunk0; ch < t.chunk0 + t.nchunks; ++ch)
+                    for (int32_t i = 0; i < 32; ++i) w += hp.slot_len[(size_t)ch * 32 + i];
+                return w + 32;   // a little per-tile overhead
+            };
+            std::vector<std::vector<Tile>> q((size_t)nq);
+            int64_t total = 0;
+            std::vector<int64_t> w(hp.tiles.size());
+            for (size_t i = 0; i < hp.tiles.size(); ++i) {
+                w[i] = weight(hp.tiles[i]);
+                if (hp.tiles[i].kind != TILE_CHUNK) total += w[i];
+            }
+            int32_t rr = 0;
+            for (size_t i = 0; i < hp.tiles.size(); ++i)
+                if (hp.tiles[i].kind == TILE_CHUNK) q[(size_t)(rr++ % nq)].push_back(hp.tiles[i]);
+            int64_t acc = 0;
+            for (size_t i = 0; i < hp.tiles.size(); ++i) {
+                if (hp.tiles[i].kind == TILE_CHUNK) continue;
+                // queue index by the tile's midpoint in the nonzero sequence
+                const int64_t mid = acc + w[i] / 2;
+                const int32_t k = (int32_t)std::min<int64_t>(nq - 1, total ? mid * nq / total : 0);
+                q[(size_t)k].push_back(hp.tiles[i]);
+                acc += w[i];
+            }
+            std::vector<Tile> ordered;
+            ordered.reserve(hp.tiles.size());
+            qbeg.assign((size_t)nq + 1, 0);
+            for (int32_t k = 0; k < nq; ++k) {
+                qbeg[k] = (int32_t)ordered.size();
+                ordered.insert(ordered.end(), q[k].begin(), q[k].end());
+            }
+            qbeg[nq] = (int32_t)ordered.size();
+            hp.tiles.swap(ordered);
+        }
+
         Arena a;
         if (!tiled) add_vec(a, hp.rowptr, (const void **)&dp.rowptr);
         add_vec(a, hp.col32, (const void **)&dp.col32);
@@ -174,7 +235,14 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
             if (!hp.fixups.empty()) add_vec(a, hp.fixups, (const void **)&dp.fixups);
             if (hp.partial_slots > 0)
                 a.add(nullptr, (size_t)hp.partial_slots * r * xb, &dp.partial);
+            if (nq > 0) {
+                add_vec(a, qbeg, (const void **)&dp.qbeg);
+                a.add(nullptr, sizeof(int32_t) * ((size_t)nq + 1), (void **)&dp.qcount, true);
+            } else if (hp.flags & SPMV_FLAG_PERSISTENT) {
+                a.add(nullptr, 2 * sizeof(int32_t), (void **)&dp.ctr, true);
+            }
         }
+        a.add(nullptr, sizeof(int32_t), (void **)&dp.status, true);
         if (!hp.row_perm.empty()) add_vec(a, hp.row_perm, (const void **)&p->d_row_perm);
         if (!hp.col_perm.empty()) add_vec(a, hp.col_perm, (const void **)&p->d_col_perm);
 
@@ -196,6 +264,13 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
                     spmv_plan_destroy(p);
                     return s;
                 }
+            } else if (it.zero && it.bytes) {
+                e = cudaMemset(d, 0, it.bytes);
+                if (e != cudaSuccess) {
+                    spmv_status s = cuda_fail(e, "clear");
+                    spmv_plan_destroy(p);
+                    return s;
+                }
             }
             off += (it.bytes + 255) & ~size_t(255);
         }
@@ -209,7 +284,16 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         dp.n_long = (int32_t)hp.long_rows.size();
         dp.n_tiles = (int32_t)hp.tiles.size();
         dp.n_fixups = (int32_t)hp.fixups.size();
-        dp.smem_bytes = any_staged ? hp.tile_cols * r * xb : 0;
+        dp.smem_bytes = any_staged ? (hp.max_staged * r * xb + 15) / 16 * 16 : 0;
+        dp.nq = nq;
+        if (tiled) {
+            e = cudaDeviceGetAttribute(&dp.n_sm, cudaDevAttrMultiProcessorCount, p->device);
+            if (e != cudaSuccess) {
+                spmv_status s = cuda_fail(e, "cudaDeviceGetAttribute");
+                spmv_plan_destroy(p);
+                return s;
+            }
+        }
 
         // info
         spmv_plan_info &I = p->info;
@@ -325,10 +409,35 @@ extern "C" spmv_status spmv_exec(spmv_plan *plan, const void *x_hat, void *y_hat
         set_error("NULL vector");
         return SPMV_E_INVALID;
     }
+    if (reinterpret_cast<uintptr_t>(x_hat) % 16 != 0) {
+        set_error("x_hat is not 16-byte aligned");
+        return SPMV_E_INVALID;
+    }
     spmv_status st = device_matches(plan);
     if (st != SPMV_OK) return st;
     cudaError_t e = run(plan, x_hat, y_hat, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "spmv kernel launch");
+    return SPMV_OK;
+}
+
+extern "C" spmv_status spmv_plan_check(spmv_plan *plan, void *stream)
+{
+    clear_error();
+    if (!plan) {
+        set_error("plan is NULL");
+        return SPMV_E_INVALID;
+    }
+    spmv_status st = device_matches(plan);
+    if (st != SPMV_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, plan->dp.status, sizeof(flag), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the plan status");
+    if (flag) {
+        set_error("a bounded device wait gave up in an earlier spmv_exec: its y_hat is incomplete");
+        return SPMV_E_TIMEOUT;
+    }
     return SPMV_OK;
 }
 
@@ -354,6 +463,16 @@ extern "C" spmv_status spmv_exec_host(spmv_plan *plan, const void *x_hat_host, v
             return SPMV_E_NOMEM;
         }
     }
+    if (!plan->h_status) {
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void **>(&plan->h_status), sizeof(int32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            plan->h_status = nullptr;
+            set_error("pinned host allocation of the status word failed");
+            return SPMV_E_NOMEM;
+        }
+        *plan->h_status = 0;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(plan->io_x, x_hat_host, plan->xbytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy of x to the device");
@@ -361,8 +480,14 @@ extern "C" spmv_status spmv_exec_host(spmv_plan *plan, const void *x_hat_host, v
     if (e != cudaSuccess) return cuda_fail(e, "spmv kernel launch");
     e = cudaMemcpyAsync(y_hat_host, plan->io_y, plan->ybytes, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy of y to the host");
+    e = cudaMemcpyAsync(plan->h_status, plan->dp.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the plan status");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (*plan->h_status) {
+        set_error("a bounded device wait gave up: y_hat is incomplete");
+        return SPMV_E_TIMEOUT;
+    }
     return SPMV_OK;
 }
 
@@ -403,6 +528,107 @@ extern "C" spmv_status spmv_unpermute_y(const spmv_plan *plan, const void *y_hat
     return permute_common(plan, y_hat, y, false, stream);
 }
 
+extern "C" spmv_status spmv_plan_autotune(const spmv_csr *A, const spmv_perm *perm,
+                                          const spmv_splits *splits,
+                                          const spmv_opts *candidates, int32_t n_candidates,
+                                          int32_t reps, void *stream, spmv_plan **out,
+                                          int32_t *best, float *best_ms)
+{
+    clear_error();
+    if (!out || !candidates || n_candidates < 1) {
+        set_error("autotune needs an output and at least one candidate");
+        return SPMV_E_INVALID;
+    }
+    *out = nullptr;
+    if (reps < 1) reps = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    spmv_plan *keep = nullptr;
+    float keep_ms = 0.0f;
+    int32_t keep_i = -1;
+    void *xb = nullptr, *yb = nullptr;
+    spmv_plan *owner = nullptr;          // plan whose allocator holds xb / yb
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    spmv_status st = SPMV_OK;
+    auto fail_cuda = [&](cudaError_t e, const char *what) {
+        st = cuda_fail(e, what);
+        return st;
+    };
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreate");
+    for (int32_t i = 0; i < n_candidates && st == SPMV_OK; ++i) {
+        spmv_plan *p = nullptr;
+        st = spmv_plan_create(A, perm, splits, &candidates[i], &p);
+        if (st != SPMV_OK) break;
+        if (!xb) {
+            // zero vectors sized for any candidate (same m, n; widest r)
+            size_t xbytes = 0, ybytes = 0;
+            for (int32_t j = 0; j < n_candidates; ++j) {
+                const int rj = candidates[j].nrhs > 0 ? candidates[j].nrhs : 1;
+                const size_t el = candidates[j].dtype == SPMV_F64 ? 8 : 4;
+                xbytes = std::max(xbytes, (size_t)A->n * rj * el);
+                ybytes = std::max(ybytes, (size_t)A->m * rj * el);
+            }
+            owner = p;
+            xb = dev_alloc(p, xbytes);
+            yb = dev_alloc(p, ybytes);
+            if (!xb || !yb) {
+                set_error("device allocation for autotuning failed");
+                st = SPMV_E_NOMEM;
+                spmv_plan_destroy(p);
+                owner = nullptr;
+                break;
+            }
+            if ((e = cudaMemsetAsync(xb, 0, xbytes, s)) != cudaSuccess) {
+                fail_cuda(e, "clear x");
+                break;
+            }
+        }
+        // one warm call, then reps timed calls
+        if ((e = run(p, xb, yb, s)) != cudaSuccess || (e = cudaEventRecord(e0, s)) != cudaSuccess) {
+            fail_cuda(e, "autotune launch");
+            spmv_plan_destroy(p);
+            break;
+        }
+        for (int32_t k = 0; k < reps && e == cudaSuccess; ++k) e = run(p, xb, yb, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            fail_cuda(e, "autotune timing");
+            spmv_plan_destroy(p);
+            break;
+        }
+        ms /= (float)reps;
+        if (!keep || ms < keep_ms) {
+            if (keep && keep != owner) spmv_plan_destroy(keep);
+            keep = p;
+            keep_ms = ms;
+            keep_i = i;
+        } else if (p != owner) {
+            spmv_plan_destroy(p);
+        }
+    }
+    // the scratch vectors belong to the first plan's allocator
+    if (owner) {
+        cudaStreamSynchronize(s);
+        dev_free(owner, xb);
+        dev_free(owner, yb);
+        if (owner != keep) spmv_plan_destroy(owner);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPMV_OK) {
+        if (keep) spmv_plan_destroy(keep);
+        return st;
+    }
+    *out = keep;
+    if (best) *best = keep_i;
+    if (best_ms) *best_ms = keep_ms;
+    return SPMV_OK;
+}
+
 extern "C" spmv_status spmv_plan_get_info(const spmv_plan *plan, spmv_plan_info *info)
 {
     clear_error();
@@ -423,6 +649,7 @@ extern "C" spmv_status spmv_plan_destroy(spmv_plan *plan)
     dev_free(plan, plan->io_x);
     dev_free(plan, plan->io_y);
     dev_free(plan, plan->arena);
+    if (plan->h_status) cudaFreeHost(plan->h_status);
     delete plan;
     if (e != cudaSuccess) return cuda_fail(e, "synchronize before destroy");
     return SPMV_OK;

@@ -28,6 +28,14 @@ struct DevPlan {
     const Fixup *fixups = nullptr;
     int32_t n_fixups = 0;
     int32_t smem_bytes = 0;            // staged x entries
+    // SM-affine schedule (nq = 0: one CTA per tile in tile order)
+    const int32_t *qbeg = nullptr;     // nq + 1
+    int32_t *qcount = nullptr;         // nq + 1 counters, zero between launches
+    int32_t nq = 0;
+    int32_t *status = nullptr;         // 1 after a bounded device wait gave up
+    // persistent schedule (ctr = NULL: one CTA per tile)
+    int32_t *ctr = nullptr;            // next-tile counter, finished-CTA counter
+    int32_t n_sm = 0;
 };
 
 cudaError_t exec_f64(const DevPlan &P, const void *x, void *y, cudaStream_t s);

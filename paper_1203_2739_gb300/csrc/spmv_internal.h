@@ -86,16 +86,22 @@ struct HostPlan {
     int64_t partial_slots = 0;
     int32_t n_chunk_tiles = 0, n_staged_tiles = 0, n_global_tiles = 0;
     int64_t staged_entries = 0, list_entries = 0, direct_nnz = 0, narrow_nnz = 0;
+    int32_t max_staged = 0;        // most x entries one tile stages
     int64_t padded_elems = 0;      // stored elements (with padding) in chunks
     int64_t fma_slots = 0;         // sum over chunks of 32 * (longest row)
 
     std::vector<int32_t> row_perm, col_perm;  // empty = identity
 };
 
-// Build the host image (validation, P_r A P_c, split, tiling).
+// Build the host image (validation, P_r A P_c, split, tiling).  n_sm: the
+// device's SM count, which sets the default tile size (0 = 152, GB300).
 spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
                             const spmv_splits *splits, const spmv_opts *opts,
-                            HostPlan *out);
+                            int32_t n_sm, HostPlan *out);
+
+// Resident CTAs per SM the tiled kernel is sized for (its register budget
+// asks for at least this many).
+constexpr int32_t kTileCtasPerSm = 6;
 
 // Round-to-nearest-even FP64 -> BF16 bits.
 uint16_t bf16_rne(double v);

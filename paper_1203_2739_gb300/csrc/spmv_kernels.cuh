@@ -27,8 +27,10 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "spmv_device.h"
@@ -48,6 +50,11 @@ constexpr int kThreads = 256;
 #endif
 #ifndef SPMV_TILE_MINBLOCKS
 #define SPMV_TILE_MINBLOCKS 6
+#endif
+//   SPMV_CHUNK_PAIR   1 = a warp works on two chunks of 32 rows at once
+//                     (single right-hand side)
+#ifndef SPMV_CHUNK_PAIR
+#define SPMV_CHUNK_PAIR 0
 #endif
 
 // loads of the matrix stream, read exactly once per SpMV
@@ -138,6 +145,47 @@ __device__ __forceinline__ void block_sum(T (&s)[R])
     }
 }
 
+// ------------------------------------------- bulk copies into shared memory --
+// The staged run of a tile is one contiguous range of x_hat: one thread
+// hands it to the TMA engine as a single bulk copy (cp.async.bulk) that
+// signals an mbarrier, instead of every thread loading and storing entries.
+// Waits are bounded: after kWaitLimit polls the CTA gives up, raises a flag
+// the host reads (SPMV_E_TIMEOUT) and skips the tile.
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar)
+{
+    // order earlier generic-proxy reads of the destination (a previous tile)
+    // before the async-proxy writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
+{
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(smem_addr(bar)), "r"(phase) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------ plain CSR, vector per row --
 template <int LANES, int R, typename VT, typename XT>
 __global__ void __launch_bounds__(kThreads)
@@ -195,22 +243,48 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
 }
 
 // ----------------------------------------------------------- tiled kernel --
-// One CTA per tile.  After staging, warp w takes chunks w, w+8, ...; lane i
-// owns row i of the chunk and runs one FMA chain over its row: element k of
-// the chunk's rows sits at chunk_off + 32 k + i, so every load is coalesced
-// and every FP64 FMA runs with the lanes of all rows still going.
+template <typename VT, typename XT>
+struct TileArgs {
+    const Tile *tiles;
+    const int32_t *chunk_off, *slot_dst, *slot_len;
+    const VRow *vrows;
+    const uint16_t *c16;
+    const int32_t *c32;
+    const VT *val;
+    const int32_t *xlist;
+    const XT *x;
+    XT *y, *partial;
+    // SM-affine schedule: tiles of queue q are qbeg[q] .. qbeg[q+1]-1
+    const int32_t *qbeg;
+    int32_t *qcount;        // nq claim counters, then one finished-CTA counter
+    int32_t nq;
+    int32_t *status;        // set to 1 when a bounded wait gives up
+};
+
+// One tile.  After staging, warp w takes chunks w, w+8, ...; lane i owns row
+// i of the chunk and runs one FMA chain over its row: element k of the
+// chunk's rows sits at chunk_off + 32 k + i, so every load is coalesced and
+// every FP64 FMA runs with the lanes of all rows still going.
+// Returns false when the staging copy did not complete within the wait limit
+// (the tile is then skipped and A.status raised).  `bar` is the CTA's
+// mbarrier, `phase` its current parity.
 template <int R, typename VT, typename XT>
-__global__ void __launch_bounds__(kThreads, SPMV_TILE_MINBLOCKS)
-k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
-        const int32_t *__restrict__ slot_dst, const int32_t *__restrict__ slot_len,
-        const VRow *__restrict__ vrows, const uint16_t *__restrict__ c16,
-        const int32_t *__restrict__ c32,
-        const VT *__restrict__ val, const int32_t *__restrict__ xlist,
-        const XT *__restrict__ x, XT *__restrict__ y, XT *__restrict__ partial)
+__device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> &A,
+                                          uint64_t *bar, uint32_t &phase)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     XT *seg = reinterpret_cast<XT *>(smem_raw);
-    const Tile t = tiles[blockIdx.x];
+    const int32_t *__restrict__ chunk_off = A.chunk_off;
+    const int32_t *__restrict__ slot_dst = A.slot_dst;
+    const int32_t *__restrict__ slot_len = A.slot_len;
+    const VRow *__restrict__ vrows = A.vrows;
+    const uint16_t *__restrict__ c16 = A.c16;
+    const int32_t *__restrict__ c32 = A.c32;
+    const VT *__restrict__ val = A.val;
+    const int32_t *__restrict__ xlist = A.xlist;
+    const XT *__restrict__ x = A.x;
+    XT *__restrict__ y = A.y;
+    XT *__restrict__ partial = A.partial;
 
     if (t.kind == TILE_CHUNK) {
         XT s[R];
@@ -227,24 +301,58 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
 #pragma unroll
             for (int c = 0; c < R; ++c) partial[(int64_t)t.slot * R + c] = s[c];
         }
-        return;
+        return true;
     }
 
     const int kind = t.kind;
     if (kind != TILE_GLOBAL) {
-        // stage the reused x entries: the contiguous run, then the list
-        for (int32_t i = threadIdx.x; i < t.runlen; i += kThreads) {
-            const int64_t src = (int64_t)(t.run0 + i) * R;
+        // stage the reused x entries: the contiguous run (one bulk copy of
+        // its 16-byte-aligned body; the plan aligns the run's start and its
+        // end unless it ends at x's end), then the gathered list
+        const int32_t run_elems = t.runlen * R;
+        const uint32_t body = (uint32_t)(run_elems * (int32_t)sizeof(XT)) & ~15u;
+        if (threadIdx.x == 0 && body > 0)
+            bulk_copy_g2s(seg, x + (int64_t)t.run0 * R, body, bar);
+        for (int32_t i = (int32_t)(body / sizeof(XT)) + threadIdx.x; i < run_elems; i += kThreads)
+            seg[i] = __ldg(x + (int64_t)t.run0 * R + i);
+        // list: batches of 8 entries per thread, every index load issued
+        // before the gathers that depend on them
+        constexpr int LB = R == 1 ? 8 : (R == 2 ? 4 : (R == 4 ? 2 : 1));
+        for (int32_t i0 = 0; i0 < t.listlen; i0 += LB * kThreads) {
+            int32_t src[LB];
 #pragma unroll
-            for (int c = 0; c < R; ++c) seg[i * R + c] = __ldg(x + src + c);
-        }
-        for (int32_t i = threadIdx.x; i < t.listlen; i += kThreads) {
-            const int64_t src = (int64_t)__ldg(xlist + t.list0 + i) * R;
-            const int32_t d = (t.runlen + i) * R;
+            for (int u = 0; u < LB; ++u) {
+                const int32_t i = i0 + u * kThreads + (int32_t)threadIdx.x;
+                src[u] = i < t.listlen ? __ldg(xlist + t.list0 + i) : -1;
+            }
+            XT v[LB][R];
 #pragma unroll
-            for (int c = 0; c < R; ++c) seg[d + c] = __ldg(x + src + c);
+            for (int u = 0; u < LB; ++u)
+#pragma unroll
+                for (int c = 0; c < R; ++c)
+                    v[u][c] = src[u] >= 0 ? __ldg(x + (int64_t)src[u] * R + c) : XT(0);
+#pragma unroll
+            for (int u = 0; u < LB; ++u) {
+                const int32_t i = i0 + u * kThreads + (int32_t)threadIdx.x;
+                if (i < t.listlen) {
+#pragma unroll
+                    for (int c = 0; c < R; ++c) seg[(t.runlen + i) * R + c] = v[u][c];
+                }
+            }
         }
-        __syncthreads();
+        bool ok = true;
+        if (body > 0) ok = mbar_wait(bar, phase);
+        ok = __syncthreads_and(ok);
+        if (body > 0) phase ^= 1u;
+        if (!ok) {
+            // the copy is still owed to this barrier: wait once more (bounded)
+            // before the CTA leaves, then report
+            if (threadIdx.x == 0) {
+                atomicExch(A.status, 1);
+                mbar_wait(bar, phase ^ 1u);
+            }
+            return false;
+        }
     }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -298,12 +406,68 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
         if (lane == 0) store(row.dst, s);
     }
 
-    // chunks of 32 rows, one lane per row, batches of U elements per lane
-    for (int32_t ch = t.chunk0 + warp; ch < t.chunk0 + t.nchunks; ch += kThreads / 32) {
-        const int32_t slot = ch * 32 + lane;
-        const int32_t len = __ldg(slot_len + slot);
+#if SPMV_CHUNK_PAIR
+    if (R == 1) {
+        // two neighbouring chunks per warp at a time: twice the independent
+        // loads and gathers in flight per lane
+        constexpr int UP = 4;
+        const int32_t cend = t.chunk0 + t.nchunks;
+        for (int32_t ch = t.chunk0 + 2 * warp; ch < cend; ch += 2 * (kThreads / 32)) {
+            const bool hasb = ch + 1 < cend;
+            const int32_t slota = ch * 32 + lane, slotb = slota + 32;
+            const int32_t lena = __ldg(slot_len + slota);
+            const int32_t lenb = hasb ? __ldg(slot_len + slotb) : 0;
+            const int64_t offa = __ldg(chunk_off + ch) + lane;
+            const int64_t offb = hasb ? __ldg(chunk_off + ch + 1) + lane : 0;
+            const int32_t L = __shfl_sync(0xffffffffu, max(lena, lenb), 0);
+            XT sa[R] = {XT(0)}, sb[R] = {XT(0)};
+            for (int32_t k0 = 0; k0 < L; k0 += UP) {
+                XT va[UP], vb[UP];
+                int32_t ca[UP], cb[UP];
+#pragma unroll
+                for (int u = 0; u < UP; ++u) {
+                    const bool ona = k0 + u < lena, onb = k0 + u < lenb;
+                    const int64_t ea = offa + (int64_t)(k0 + u) * 32;
+                    const int64_t eb = offb + (int64_t)(k0 + u) * 32;
+                    va[u] = ona ? (XT)load_val(val + ea) : XT(0);
+                    ca[u] = ona ? colat(ea) : 0;
+                    vb[u] = onb ? (XT)load_val(val + eb) : XT(0);
+                    cb[u] = onb ? colat(eb) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < UP; ++u) {
+                    if (k0 + u < lena) sa[0] = fma(va[u], xat(ca[u], 0), sa[0]);
+                    if (k0 + u < lenb) sb[0] = fma(vb[u], xat(cb[u], 0), sb[0]);
+                }
+            }
+            store(__ldg(slot_dst + slota), sa);
+            if (hasb) store(__ldg(slot_dst + slotb), sb);
+        }
+        return true;
+    }
+#endif
+    // chunks of 32 rows, one lane per row, batches of U elements per lane.
+    // A chunk's metadata (row length, destination, offset) is loaded one
+    // chunk ahead, so a chunk costs two dependent trips to memory (its
+    // stream, then its gathers) instead of four.
+    const int32_t cend = t.chunk0 + t.nchunks;
+    int32_t ch = t.chunk0 + warp;
+    int32_t len_n = 0, dst_n = -1, off_n = 0;
+    if (ch < cend) {
+        len_n = __ldg(slot_len + ch * 32 + lane);
+        dst_n = __ldg(slot_dst + ch * 32 + lane);
+        off_n = __ldg(chunk_off + ch);
+    }
+    for (; ch < cend; ch += kThreads / 32) {
+        const int32_t len = len_n, dst = dst_n;
+        const int64_t off = (int64_t)off_n + lane;
+        const int32_t chn = ch + kThreads / 32;
+        if (chn < cend) {
+            len_n = __ldg(slot_len + chn * 32 + lane);
+            dst_n = __ldg(slot_dst + chn * 32 + lane);
+            off_n = __ldg(chunk_off + chn);
+        }
         const int32_t L = __shfl_sync(0xffffffffu, len, 0);   // rows sorted: lane 0 is longest
-        const int64_t off = __ldg(chunk_off + ch) + lane;
         XT s[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) s[c] = XT(0);
@@ -325,7 +489,152 @@ k_tiles(const Tile *__restrict__ tiles, const int32_t *__restrict__ chunk_off,
                 }
             }
         }
-        store(__ldg(slot_dst + slot), s);
+        store(dst, s);
+    }
+    return true;
+}
+
+// One CTA per tile, in tile order.
+template <int R, typename VT, typename XT>
+__global__ void __launch_bounds__(kThreads, SPMV_TILE_MINBLOCKS)
+k_tiles(const TileArgs<VT, XT> A)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    const Tile t = A.tiles[blockIdx.x];
+    tile_work<R, VT, XT>(t, A, &bar, phase);
+}
+
+// Persistent CTAs, one per resident slot, claiming tiles in tile order from
+// one counter.  The first tile of CTA b is tile b; each further claim is an
+// atomic issued at the start of the current tile, so its latency hides
+// behind the tile's work.  No CTA waits for another.  The last CTA out resets
+// the counters for the next launch.
+template <int R, typename VT, typename XT>
+__global__ void __launch_bounds__(kThreads, SPMV_TILE_MINBLOCKS)
+k_tiles_persist(const TileArgs<VT, XT> A, const int32_t n_tiles, int32_t *ctr)
+{
+    __shared__ int32_t claim;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    int32_t cur = (int32_t)blockIdx.x;
+    while (cur < n_tiles) {
+        int32_t nxt = 0;
+        if (threadIdx.x == 0) nxt = (int32_t)gridDim.x + atomicAdd(ctr, 1);
+        if (!tile_work<R, VT, XT>(A.tiles[cur], A, &bar, phase)) break;
+        __syncthreads();                // every warp is done with this tile
+        if (threadIdx.x == 0) claim = nxt;
+        __syncthreads();
+        cur = claim;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int32_t done = atomicAdd(ctr + 1, 1);
+        if (done == (int32_t)(gridDim.x - 1)) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t sm_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t sm_id_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(r));
+    return r;
+}
+
+// Persistent CTAs with an SM-affine schedule.  The plan cuts the tile
+// sequence (tiles of a part are consecutive) into one queue per SM; a CTA
+// first drains the queue of the SM it runs on, so every CTA on that SM works
+// on the same part and the part's x window stays in the SM's L1 -- the
+// per-SM cache the partition was sized for.  Then it helps the other queues:
+// the whole CTA reads every queue's counter at once and claims from the
+// queue with the most tiles left, so all tiles are done however the CTAs were
+// placed, at one round trip per steal.  Claims are atomic counters (no
+// waiting); the last CTA to finish resets them for the next call.
+template <int R, typename VT, typename XT>
+__global__ void __launch_bounds__(kThreads, SPMV_TILE_MINBLOCKS)
+k_tiles_affine(const TileArgs<VT, XT> A)
+{
+    __shared__ int32_t claim, claim_q;
+    __shared__ int32_t best_left[kThreads / 32], best_q[kThreads / 32];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar);
+    uint32_t phase = 0;
+    const int32_t nq = A.nq;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t q = (int32_t)(((uint64_t)sm_id() * (uint64_t)nq) / max(1u, sm_id_count()));
+    for (;;) {
+        __syncthreads();                // the previous tile is done with shared memory
+        if (threadIdx.x == 0) {
+            const int32_t b = __ldg(A.qbeg + q), len = __ldg(A.qbeg + q + 1) - b;
+            const int32_t i = atomicAdd(A.qcount + q, 1);
+            claim = i < len ? b + i : -1;
+        }
+        __syncthreads();
+        const int32_t ti = claim;
+        if (ti >= 0) {
+            if (!tile_work<R, VT, XT>(A.tiles[ti], A, &bar, phase)) break;
+            continue;
+        }
+        // this queue is drained: find the one with the most unclaimed tiles
+        int32_t left = 0, lq = -1;
+        for (int32_t k = threadIdx.x; k < nq; k += kThreads) {
+            const int32_t len = __ldg(A.qbeg + k + 1) - __ldg(A.qbeg + k);
+            const int32_t l = len - *((volatile int32_t *)(A.qcount + k));
+            if (l > left) {
+                left = l;
+                lq = k;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const int32_t l2 = __shfl_xor_sync(0xffffffffu, left, off);
+            const int32_t q2 = __shfl_xor_sync(0xffffffffu, lq, off);
+            if (l2 > left || (l2 == left && q2 > lq)) {
+                left = l2;
+                lq = q2;
+            }
+        }
+        if (lane == 0) {
+            best_left[warp] = left;
+            best_q[warp] = lq;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t bl = 0, bq = -1;
+            for (int w = 0; w < kThreads / 32; ++w)
+                if (best_left[w] > bl) {
+                    bl = best_left[w];
+                    bq = best_q[w];
+                }
+            claim_q = bq;
+        }
+        __syncthreads();
+        if (claim_q < 0) break;         // every queue is drained
+        q = claim_q;
+    }
+    // the last CTA out resets the claim counters for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int32_t done = atomicAdd(A.qcount + nq, 1);
+        if (done == (int32_t)(gridDim.x - 1)) {
+            for (int32_t k = 0; k < nq; ++k) A.qcount[k] = 0;
+            A.qcount[nq] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -370,6 +679,31 @@ inline cudaError_t ensure_smem(Kern k, int bytes)
     return e;
 }
 
+// CTAs of a kernel resident per SM at a given dynamic shared memory size,
+// cached per (kernel, device, size).
+template <class Kern>
+inline cudaError_t resident_ctas(Kern k, int smem, int *out)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int>, int> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(reinterpret_cast<const void *>(k), dev, smem);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    cache[key] = n;
+    *out = n;
+    return cudaSuccess;
+}
+
 template <int LANES, int R, typename VT, typename XT>
 cudaError_t launch_k1(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
 {
@@ -386,12 +720,50 @@ template <int R, typename VT, typename XT>
 cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
 {
     if (P.n_tiles > 0) {
-        auto kern = k_tiles<R, VT, XT>;
-        cudaError_t e = ensure_smem(kern, P.smem_bytes);
-        if (e != cudaSuccess) return e;
-        kern<<<(unsigned)P.n_tiles, kThreads, P.smem_bytes, s>>>(
-            P.tiles, P.chunk_off, P.slot_dst, P.slot_len, P.vrows, P.col16, P.col32,
-            static_cast<const VT *>(P.val), P.xlist, x, y, static_cast<XT *>(P.partial));
+        TileArgs<VT, XT> A;
+        A.tiles = P.tiles;
+        A.chunk_off = P.chunk_off;
+        A.slot_dst = P.slot_dst;
+        A.slot_len = P.slot_len;
+        A.vrows = P.vrows;
+        A.c16 = P.col16;
+        A.c32 = P.col32;
+        A.val = static_cast<const VT *>(P.val);
+        A.xlist = P.xlist;
+        A.x = x;
+        A.y = y;
+        A.partial = static_cast<XT *>(P.partial);
+        A.qbeg = P.qbeg;
+        A.qcount = P.qcount;
+        A.nq = P.nq;
+        A.status = P.status;
+        cudaError_t e;
+        if (P.nq > 0) {
+            auto kern = k_tiles_affine<R, VT, XT>;
+            e = ensure_smem(kern, P.smem_bytes);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            e = resident_ctas(kern, P.smem_bytes, &per_sm);
+            if (e != cudaSuccess) return e;
+            const int64_t grid = std::min<int64_t>((int64_t)P.nq * std::max(per_sm, 1),
+                                                   (int64_t)P.n_tiles);
+            kern<<<(unsigned)grid, kThreads, P.smem_bytes, s>>>(A);
+        } else if (P.ctr != nullptr) {
+            auto kern = k_tiles_persist<R, VT, XT>;
+            e = ensure_smem(kern, P.smem_bytes);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            e = resident_ctas(kern, P.smem_bytes, &per_sm);
+            if (e != cudaSuccess) return e;
+            const int64_t grid = std::min<int64_t>((int64_t)P.n_sm * std::max(per_sm, 1),
+                                                   (int64_t)P.n_tiles);
+            kern<<<(unsigned)grid, kThreads, P.smem_bytes, s>>>(A, P.n_tiles, P.ctr);
+        } else {
+            auto kern = k_tiles<R, VT, XT>;
+            e = ensure_smem(kern, P.smem_bytes);
+            if (e != cudaSuccess) return e;
+            kern<<<(unsigned)P.n_tiles, kThreads, P.smem_bytes, s>>>(A);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

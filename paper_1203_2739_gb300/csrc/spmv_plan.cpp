@@ -205,22 +205,30 @@ namespace {
 
 struct TileCfg {
     int32_t W;          // staging capacity (x entries)
-    int32_t tnnz;       // nonzero budget of a staging tile
-    int32_t gnnz;       // nonzero budget of a tile that stages nothing
+    int32_t align;      // staged runs start and end on multiples of this (16 bytes)
+    int32_t n;          // columns (a run may end at n unaligned)
+    int32_t tnnz;       // nonzero budget of a tile
     int32_t long_t;     // rows longer than this become chunks
     int32_t chunk;      // nonzeros per chunk of a long row
     int32_t max_rows;   // rows per tile
     int32_t vrow_len;   // rows longer than this are reduced by a whole warp
+    int32_t entry_bytes;  // bytes of one x entry (r values)
+    int32_t list_min;   // uses in the tile that put a column outside the run on the list
     bool stage;         // staging allowed
 };
 
-// Cuts the plan rows of one part into tiles.  A tile keeps adding rows while
-// the x entries it reuses (touched at least twice) still fit the staging
-// capacity W -- the shared-memory version of "every R_k fits into the cache"
-// (Theorem 1).  At the end each column of the tile is either staged (inside
-// the part's contiguous home range, or reused) or gathered directly from L2
-// (touched once, outside the home range), and the tile's rows are sorted by
-// length into chunks of 32 stored column-major.
+// Cuts the plan rows of the parts into tiles of consecutive rows with a
+// fixed nonzero budget, and gives each tile the part of the paper's "cache"
+// a CTA owns: shared memory for W x entries (Theorem 1 asks that every part
+// fit the cache; here the tile stages what fits and gathers the rest).  Two
+// staging sets are weighed: (a) the span of home columns the tile uses --
+// the C_k of its parts, a contiguous range of x_hat copied in bulk -- plus
+// the border columns it uses often (list_min times or more), or (b) the
+// columns it uses often, most used first, up to W.  A gathered x entry costs
+// one L2 request per use; a staged one costs a 128-byte line per 128 bytes of
+// run (one request per list entry) and nothing per use.  The tile takes the
+// set that saves more requests, if it saves at least what it costs.  Rows
+// are sorted by length into chunks of 32 stored column-major.
 struct Tiler {
     const TileCfg cfg;
     const std::vector<int32_t> &prp;   // plan row starts
@@ -239,6 +247,17 @@ struct Tiler {
         : cfg(c), prp(rp), col(cl), pval(pv), pdst(pd), P(plan), mark((size_t)n, -1),
           cnt((size_t)n, 0), loc((size_t)n, 0) {}
 
+    // the aligned run covering home columns [lo, hi]
+    void aligned_run(int32_t lo, int32_t hi, int32_t *run0, int32_t *runlen) const
+    {
+        const int32_t a = cfg.align;
+        const int32_t b = lo - lo % a;
+        int64_t e = (int64_t)hi + 1;
+        e = std::min<int64_t>(cfg.n, (e + a - 1) / a * a);
+        *run0 = b;
+        *runlen = (int32_t)(e - b);
+    }
+
     // Close the tile made of plan rows `rows`; its columns carry mark == stamp
     // and their use counts in cnt.
     void emit(const std::vector<int32_t> &rows, int64_t tile_nnz, int32_t h0, int32_t h1,
@@ -248,67 +267,79 @@ struct Tiler {
         Tile t{};
         t.kind = TILE_GLOBAL;
         if (cfg.stage && !force_global && tile_nnz > 0) {
-            std::sort(used.begin(), used.end());
-            int32_t lo = -1, hi = -1;
+            auto home = [&](int32_t c) { return c >= h0 && c < h1; };
+            // option (a): the run over the used home columns + reused border
+            int32_t lo = INT32_MAX, hi = -1;
             for (int32_t c : used)
-                if (c >= h0 && c < h1 && cnt[c] >= 2) {
-                    if (lo < 0) lo = c;
-                    hi = c;
+                if (home(c)) {
+                    lo = std::min(lo, c);
+                    hi = std::max(hi, c);
                 }
             int32_t run0 = 0, runlen = 0;
-            if (lo >= 0) {
-                int32_t inspan = 0;
-                for (int32_t c : used) inspan += (c >= lo && c <= hi);
-                const int32_t span = hi - lo + 1;
-                if (span <= 2 * inspan) {
-                    run0 = lo;
-                    runlen = span;
-                }
-            }
-            auto in_run = [&](int32_t c) { return runlen > 0 && c >= run0 && c < run0 + runlen; };
-            int32_t listlen = 0, direct = 0;
-            int64_t staged_uses = 0;
+            if (hi >= 0) aligned_run(lo, hi, &run0, &runlen);
+            int64_t a_list = 0, a_saved = 0;
             for (int32_t c : used) {
-                if (in_run(c)) {
-                    staged_uses += cnt[c];
-                } else if (cnt[c] >= 2) {
-                    ++listlen;
-                    staged_uses += cnt[c];
-                } else {
-                    direct += cnt[c];
+                if (hi >= 0 && c >= run0 && c < run0 + runlen) a_saved += cnt[c];
+                else if (cnt[c] >= cfg.list_min) {
+                    ++a_list;
+                    a_saved += cnt[c];
                 }
             }
-            if (runlen + listlen > cfg.W) {
-                // the run does not fit beside the reused columns: list only
-                runlen = listlen = direct = 0;
-                staged_uses = 0;
-                for (int32_t c : used) {
-                    if (cnt[c] >= 2) {
+            const double line = 128.0 / cfg.entry_bytes;   // entries per 128-byte line
+            const double a_cost = (double)runlen / line + (double)a_list;
+            const bool a_fits = hi >= 0 && runlen + a_list <= cfg.W;
+            // option (b): every column used list_min times or more, the most used first
+            std::vector<int32_t> multi;
+            for (int32_t c : used)
+                if (cnt[c] >= cfg.list_min) multi.push_back(c);
+            if ((int64_t)multi.size() > cfg.W) {
+                std::nth_element(multi.begin(), multi.begin() + cfg.W, multi.end(),
+                                 [&](int32_t x, int32_t y) {
+                                     return cnt[x] != cnt[y] ? cnt[x] > cnt[y] : x < y;
+                                 });
+                multi.resize((size_t)cfg.W);
+            }
+            std::sort(multi.begin(), multi.end());
+            int64_t b_saved = 0;
+            for (int32_t c : multi) b_saved += cnt[c];
+            const double b_cost = (double)multi.size();
+            const double a_gain = a_fits ? (double)a_saved - a_cost : -1.0;
+            const double b_gain = (double)b_saved - b_cost;
+            const bool use_a = a_fits && a_gain >= b_gain;
+            const double gain = use_a ? a_gain : b_gain;
+            const double cost = use_a ? a_cost : b_cost;
+            // stage when it saves at least as many requests as it costs: a
+            // staged entry is fetched before the tile's rows start, where its
+            // latency is not hidden
+            if (gain > 0.0 && gain >= cost) {
+                if (!use_a) run0 = runlen = 0;
+                int32_t pos = runlen, listlen = 0, direct = 0;
+                t.list0 = (int32_t)P.xlist.size();
+                for (int32_t c : used) loc[c] = -1;
+                if (use_a) {
+                    for (int32_t c : used) {
+                        if (c >= run0 && c < run0 + runlen) loc[c] = c - run0;
+                        else if (cnt[c] >= cfg.list_min) {
+                            loc[c] = pos++;
+                            P.xlist.push_back(c);
+                            ++listlen;
+                        }
+                    }
+                } else {
+                    for (int32_t c : multi) {
+                        loc[c] = pos++;
+                        P.xlist.push_back(c);
                         ++listlen;
-                        staged_uses += cnt[c];
-                    } else {
-                        direct += cnt[c];
                     }
                 }
-            }
-            const int32_t staged = runlen + listlen;
-            // stage only when the staged entries are reused on average
-            if (staged > 0 && staged <= cfg.W && (double)staged_uses >= 1.5 * (double)staged) {
+                for (int32_t c : used)
+                    if (loc[c] < 0) direct += cnt[c];
                 t.kind = direct == 0 ? TILE_NARROW : TILE_MIXED;
                 t.run0 = run0;
                 t.runlen = runlen;
-                t.list0 = (int32_t)P.xlist.size();
                 t.listlen = listlen;
-                int32_t pos = runlen;
-                for (int32_t c : used) {
-                    if (in_run(c)) loc[c] = c - run0;
-                    else if (cnt[c] >= 2) {
-                        loc[c] = pos++;
-                        P.xlist.push_back(c);
-                    } else {
-                        loc[c] = -1;
-                    }
-                }
+                const int32_t staged = runlen + listlen;
+                P.max_staged = std::max(P.max_staged, staged);
                 P.staged_entries += staged;
                 P.list_entries += listlen;
                 P.direct_nnz += direct;
@@ -380,37 +411,31 @@ struct Tiler {
         P.tiles.push_back(t);
     }
 
-    // Tile plan rows [rb, re) of one part with home columns [h0, h1).
-    // chunked[r] marks rows handled as chunks (left out of the tiles).
+    // Tile plan rows [rb, re) of one part (or consecutive parts) with home
+    // columns [h0, h1): consecutive rows up to the nonzero budget; emit()
+    // then stages what fits the capacity.  chunked[r] marks rows handled as
+    // chunks (left out of the tiles).
     void tile_rows(int32_t rb, int32_t re, int32_t h0, int32_t h1,
                    const std::vector<char> &chunked, bool force_global)
     {
-        const bool staging = cfg.stage && !force_global;
-        const int32_t limit = staging ? cfg.tnnz : cfg.gnnz;
+        const int32_t limit = cfg.tnnz;
         int64_t cur_nnz = 0;
-        int32_t multi = 0;
         std::vector<int32_t> rows;
         auto close = [&]() {
             emit(rows, cur_nnz, h0, h1, force_global);
             rows.clear();
-            cur_nnz = multi = 0;
+            cur_nnz = 0;
             used.clear();
             ++stamp;
         };
         for (int32_t r = rb; r < re; ++r) {
             if (chunked[r]) continue;
             const int32_t a = prp[r], b = prp[r + 1], len = b - a;
-            if (!rows.empty()) {
-                int32_t newmulti = 0;
-                if (staging)
-                    for (int32_t q = a; q < b; ++q) {
-                        const int32_t c = col[q];
-                        newmulti += (mark[c] == stamp && cnt[c] == 1);
-                    }
-                if (multi + newmulti > cfg.W || cur_nnz + len > limit ||
-                    (int32_t)rows.size() >= cfg.max_rows)
-                    close();
-            }
+            // fill to the budget: the row goes to the next tile when it would
+            // take this one more than half its length past it
+            if (!rows.empty() &&
+                ((int32_t)rows.size() >= cfg.max_rows || cur_nnz + len / 2 > limit))
+                close();
             rows.push_back(r);
             for (int32_t q = a; q < b; ++q) {
                 const int32_t c = col[q];
@@ -419,7 +444,6 @@ struct Tiler {
                     cnt[c] = 1;
                     used.push_back(c);
                 } else {
-                    if (cnt[c] == 1) ++multi;
                     ++cnt[c];
                 }
             }
@@ -441,7 +465,7 @@ int32_t pow2_at_least(double want, int32_t lo)
 // --------------------------------------------------------------- the plan --
 spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
                             const spmv_splits *splits, const spmv_opts *opts,
-                            HostPlan *P)
+                            int32_t n_sm, HostPlan *P)
 {
     spmv_status st = validate_csr(A);
     if (st != SPMV_OK) return st;
@@ -470,8 +494,9 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     const int64_t nnz = A->nnz;
     const int xb = (o.dtype == SPMV_F64) ? 8 : 4;
     const int r = o.nrhs;
-    // shared memory of a CTA: the staged x entries
-    int32_t W = o.tile_cols > 0 ? o.tile_cols : (48 * 1024) / (xb * r);
+    // shared memory of a CTA: the staged x entries (default: 36 KB, so that
+    // kTileCtasPerSm CTAs fit an SM's 228 KB next to some L1)
+    int32_t W = o.tile_cols > 0 ? o.tile_cols : (36 * 1024) / (xb * r);
     if ((int64_t)W * xb * r > 220 * 1024 || W > 65535) {
         set_error("tile_cols=%d does not fit shared memory (x entries of %d bytes, r=%d)", W,
                   xb, r);
@@ -483,6 +508,15 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     P->form = form;
     P->dtype = o.dtype;
     P->nrhs = r;
+    if (o.flags & ~(SPMV_FLAG_NO_STAGING | SPMV_FLAG_TILED_NATURAL | SPMV_FLAG_SM_AFFINE |
+                    SPMV_FLAG_PERSISTENT)) {
+        set_error("unknown flag bits 0x%x", o.flags);
+        return SPMV_E_INVALID;
+    }
+    if ((o.flags & SPMV_FLAG_SM_AFFINE) && (o.flags & SPMV_FLAG_PERSISTENT)) {
+        set_error("SPMV_FLAG_SM_AFFINE and SPMV_FLAG_PERSISTENT exclude each other");
+        return SPMV_E_INVALID;
+    }
     P->flags = o.flags;
     P->tile_cols = W;
 
@@ -632,18 +666,24 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
 
     TileCfg cfg;
     cfg.W = W;
+    cfg.n = n;
+    cfg.entry_bytes = xb * r;
+    cfg.align = std::max(1, 16 / (xb * r));
+    cfg.list_min = 3;
     cfg.max_rows = 4096;
-    cfg.long_t = o.long_row > 0 ? o.long_row : 1024;
-    cfg.chunk = 4096;
     cfg.vrow_len = 64;
-    // tiles sized so that a launch has several waves of CTAs: about
-    // nnz / (152 SMs * 8) nonzeros each, within [2048, 8 W]
+    // tiles sized so that one launch is about one wave of resident CTAs
+    // (kTileCtasPerSm per SM): every CTA starts at once and none waits for
+    // a slot, so there is no tail wave.  Rows longer than long_t are cut into
+    // chunk tiles of the same budget (at least 4096 nonzeros); the fix-up
+    // kernel adds their pieces.
     {
-        const int64_t want = nnz / (152 * 8);
-        cfg.tnnz = o.tile_nnz > 0 ? o.tile_nnz
-                                  : (int32_t)std::min<int64_t>(std::max<int64_t>(want, 2048),
-                                                               std::max<int64_t>(8LL * W, 2048));
-        cfg.gnnz = o.tile_nnz > 0 ? o.tile_nnz : std::max<int32_t>(2048, std::min(cfg.tnnz, 8192));
+        const int64_t slots = (int64_t)(n_sm > 0 ? n_sm : 152) * kTileCtasPerSm;
+        const int64_t want = std::max<int64_t>((nnz + slots - 1) / slots, 1024);
+        cfg.tnnz = o.tile_nnz > 0 ? o.tile_nnz : (int32_t)std::min<int64_t>(want, 1 << 26);
+        cfg.chunk = std::max<int32_t>(4096, cfg.tnnz);
+        // rows up to a quarter of a tile stay in the tiles (a warp each)
+        cfg.long_t = o.long_row > 0 ? o.long_row : std::max<int32_t>(1024, cfg.tnnz / 4);
     }
     cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING);
     P->lanes = 32;                 // one lane per row, 32 rows per chunk
@@ -688,21 +728,24 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     for (int64_t q = 0; q < nnz; ++q) pval[q] = A->vals[psrc[q]];
 
     Tiler tiler(cfg, prp, pcol, pval, pdst, *P, n);
-    for (int32_t k = 0; k < K; ++k) {
+    // the parts' home columns C_1 .. C_K are consecutive ranges of x_hat, so
+    // a tile may run across part boundaries and still stage one contiguous
+    // run: the union of the C_k of the parts it covers
+    {
         int32_t h0 = 0, h1 = 0;
         if (!cp_part.empty()) {
-            h0 = cp_part[k];
-            h1 = cp_part[k + 1];
+            h0 = cp_part[0];
+            h1 = cp_part[K];
         } else if (form == SPMV_NATURAL) {
             h0 = 0;
             h1 = n;
         }
-        tiler.tile_rows(pr_part[k], pr_part[k + 1], h0, h1, chunked, false);
+        tiler.tile_rows(pr_part[0], pr_part[K], h0, h1, chunked, false);
     }
-    // DB row border R_B: x entries gathered through L2, as the paper charges
-    // every border nonzero a miss (eq. 6)
+    // DB row border R_B: no home columns (the paper charges every border
+    // nonzero a miss, eq. 6); columns it reuses may still be staged
     if (pr_part[K + 1] > pr_part[K])
-        tiler.tile_rows(pr_part[K], pr_part[K + 1], 0, 0, chunked, true);
+        tiler.tile_rows(pr_part[K], pr_part[K + 1], 0, 0, chunked, false);
 
     // long rows: contiguous, global indices, one CTA per chunk of nonzeros;
     // chunk tiles go first so the longest work starts early
@@ -729,9 +772,12 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
             chunk_tiles.push_back(t);
         }
     }
+    // row tiles first, then the chunk tiles, longest first: the smaller
+    // pieces fill the slots that free up last
     P->n_chunk_tiles = (int32_t)chunk_tiles.size();
-    chunk_tiles.insert(chunk_tiles.end(), P->tiles.begin(), P->tiles.end());
-    P->tiles.swap(chunk_tiles);
+    std::stable_sort(chunk_tiles.begin(), chunk_tiles.end(),
+                     [](const Tile &a, const Tile &b) { return a.e1 - a.e0 > b.e1 - b.e0; });
+    P->tiles.insert(P->tiles.end(), chunk_tiles.begin(), chunk_tiles.end());
     if (P->val.size() >= (size_t)INT32_MAX) {
         set_error("too many stored elements");
         return SPMV_E_UNSUPPORTED;

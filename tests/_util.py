@@ -19,6 +19,7 @@ def run_plan(S, plan, x, stream=None):
     S.spmv_permute_x(plan, xd, xh, stream)
     S.spmv_exec(plan, xh, yh, stream)
     S.spmv_unpermute_y(plan, yh, y, stream)
+    S.spmv_plan_check(plan, stream)         # no bounded device wait gave up
     torch.cuda.synchronize()
     out = y.double().cpu().numpy()
     return out.reshape(m, r) if np.ndim(x) == 2 else out

@@ -83,6 +83,10 @@ def test_plan_create_validation_before_any_device_call():
     assert _plan_status(lanes=3)[0] == S.SPMV_E_INVALID
     assert _plan_status(dtype=7)[0] == S.SPMV_E_INVALID
     assert _plan_status(tile_cols=1 << 20)[0] == S.SPMV_E_UNSUPPORTED
+    st, msg = _plan_status(flags=16)
+    assert st == S.SPMV_E_INVALID and "flag" in msg
+    st, msg = _plan_status(flags=S.SPMV_FLAG_SM_AFFINE | S.SPMV_FLAG_PERSISTENT)
+    assert st == S.SPMV_E_INVALID and "flag" in msg.lower()
     # SB: row 0 (part 0) touches column 3, which is in C_1 -> structure error
     st, msg = _plan_status(form=S.SPMV_SB, K=2, row_part_ptr=np.array([0, 3, 6, 6]),
                            col_part_ptr=np.array([0, 3, 6, 6]))

@@ -133,7 +133,7 @@ def test_split_exact(zipf, nrhs):
 
 
 # ---------------------------------------------------- kernel variants ---
-@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("flags", [1, 2, 3, 4, 5, 6, 8, 9, 10])
 def test_flag_variants(zipf, flags):
     m, n, rp, ci, v = zipf
     if flags & 2:
@@ -143,6 +143,50 @@ def test_flag_variants(zipf, flags):
     if flags & 1:
         assert plan.info["n_staged_tiles"] == 0
     _check(plan, m, n, rp, ci, v, synth.uniform_x(n, 13))
+
+
+# ------------------------------------------ staged runs (bulk copies) ---
+def _mesh_sb(nx, K, seed=0):
+    rp, ci, _ = synth.mesh5(nx, seed=seed)
+    m = n = len(rp) - 1
+    part = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_CN, K=K, seed=seed)
+    kw = dict(row_perm=part["row_perm"], col_perm=part["col_perm"], form=part["form"],
+              K=part["K"], row_part_ptr=part["row_part_ptr"], col_part_ptr=part["col_part_ptr"])
+    return m, n, rp, ci, kw
+
+
+@pytest.mark.parametrize("nx", [64, 63])          # n even, n odd (the last run ends unaligned)
+@pytest.mark.parametrize("dtype,nrhs", [(0, 1), (1, 1), (2, 1), (0, 2), (1, 8)])
+def test_staged_runs_exact(nx, dtype, nrhs):
+    m, n, rp, ci, kw = _mesh_sb(nx, 16)
+    vi = synth.integer_values(int(rp[-1]), 21)
+    plan = S.spmv_plan_create(m, n, rp, ci, vi, dtype=dtype, nrhs=nrhs, tile_nnz=2048, **kw)
+    assert plan.info["n_staged_tiles"] > 0
+    assert plan.info["smem_bytes"] % 16 == 0
+    x = synth.integer_x(n, 22, nrhs=nrhs)
+    _check(plan, m, n, rp, ci, vi, x, exact=True)
+
+
+@pytest.mark.parametrize("flags", [4, 8])
+def test_staged_runs_persistent_repeat(flags):
+    # the persistent kernels reuse one mbarrier across tiles (its phase
+    # alternates) and reset their claim counters for the next launch
+    m, n, rp, ci, kw = _mesh_sb(96, 64)
+    vi = synth.integer_values(int(rp[-1]), 23)
+    plan = S.spmv_plan_create(m, n, rp, ci, vi, tile_nnz=2048, flags=flags, **kw)
+    assert plan.info["n_staged_tiles"] > 1
+    for seed in (24, 25, 26):
+        _check(plan, m, n, rp, ci, vi, synth.integer_x(n, seed), exact=True)
+
+
+def test_misaligned_x_rejected(zipf):
+    m, n, rp, ci, v = zipf
+    plan = _sb_plan(m, n, rp, ci, v, 8, 12)
+    buf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    y = torch.zeros(m, dtype=torch.float64, device="cuda")
+    with pytest.raises(S.SpmvError, match="aligned"):
+        S.spmv_exec(plan, buf[1:], y)
+    S.spmv_plan_check(plan)
 
 
 @pytest.mark.parametrize("tile_cols,tile_nnz,long_row", [(64, 256, 32), (4096, 2048, 100),
