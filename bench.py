@@ -52,7 +52,9 @@ WORKLOAD_TEXT = {
              "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random, SB K=1024, "
              "DB K=1024, split K=4/16/64/256",
     "zipf16k": "Zipf 16384^2 (rows P(d)~d^-1.7498 on [1,512], Zipf(1.2) columns), natural vs SB",
-    "precision": "7-pt Dirichlet Laplacian 128^3, permuted",
+    "precision": "7-pt Dirichlet Laplacian 128^3, permuted; natural, random, DB K=1024 "
+                 "SpMV in the chosen dtype; CG with FP64 iterative refinement to 1e-10 "
+                 "with FP64 / FP32 / BF16 inner products",
 }
 
 
@@ -317,7 +319,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     log = (lambda s: print(s, file=sys.stderr, flush=True)) if rank == 0 else (lambda s: None)
     forms = args.forms.split(",") if args.forms else (
-        FORMS_SWEEP if args.workload == "sweep" else ["natural", "sb8", "split16"])
+        FORMS_SWEEP if args.workload == "sweep" else (
+            ["natural", "random", "db1024"] if args.workload == "precision"
+            else ["natural", "sb8", "split16"]))
     dtype = {"f64": S.SPMV_F64, "f32": S.SPMV_F32, "bf16": S.SPMV_BF16}[args.dtype]
     vb, xb = {0: (8, 8), 1: (4, 4), 2: (2, 4)}[dtype]
     tdt = torch.float64 if dtype == S.SPMV_F64 else torch.float32
@@ -330,8 +334,10 @@ def run_ours(args, rank, world, local_rank):
     for name, rp, ci, v in mats:
         m = n = len(rp) - 1
         t0 = time.perf_counter()
-        parts = partition_jobs(S, rp, ci, forms, seed=0, threads=threads,
+        need_forms = forms + (["db1024"] if args.workload == "precision" else [])
+        parts = partition_jobs(S, rp, ci, need_forms, seed=0, threads=threads,
                                cache_dir=args.partition_cache, name=name)
+        parts_kept = parts
         log("  %s: partitions %.1fs" % (name, time.perf_counter() - t0))
         for key, r in parts.items():
             log("  %s %s K=%d: partition %.1fs, cost %d (cols %d, rows %d)" % (
@@ -342,7 +348,18 @@ def run_ours(args, rank, world, local_rank):
         for f in forms:
             kw, pres = form_kwargs(S, f, rp, ci, parts)
             t1 = time.perf_counter()
-            plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, **kw)
+            chosen = None
+            if f in ("natural", "random") or args.no_autotune:
+                plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, **kw)
+            elif args.cta_threads:
+                plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype,
+                                          cta_threads=args.cta_threads, **kw)
+                chosen = "cta%d" % args.cta_threads
+            else:
+                # the tile shape is picked by measurement among the candidates
+                cands = [dict(dtype=dtype), dict(dtype=dtype, cta_threads=1024)]
+                plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v, cands, reps=5, **kw)
+                chosen = "cta1024" if cands[ibest].get("cta_threads") else "cta256"
             xh = torch.empty_like(xt)
             S.spmv_permute_x(plan, xt, xh)
             yh = torch.empty(m, dtype=tdt, device=dev)
@@ -354,10 +371,10 @@ def run_ours(args, rank, world, local_rank):
             info = plan.info
             entries.append(dict(label="%s/%s" % (name, f), plan=plan, xh=xh, yh=yh,
                                 bytes=compulsory_bytes(m, n, int(rp[-1]), vb, xb),
-                                flops=2 * int(rp[-1]), err=err, info=info,
+                                flops=2 * int(rp[-1]), err=err, info=info, tile_shape=chosen,
                                 cost=None if pres is None else int(pres["cost"])))
-            log("  plan %s/%s: K=%d tiles=%d staged=%d err=%.2e (%.1fs)" % (
-                name, f, info["K"], info["n_tiles"], info["n_staged_tiles"], err,
+            log("  plan %s/%s: K=%d tiles=%d staged=%d shape=%s err=%.2e (%.1fs)" % (
+                name, f, info["K"], info["n_tiles"], info["n_staged_tiles"], chosen, err,
                 time.perf_counter() - t1))
         del y_ref, absax
     setup_s = time.perf_counter() - t_setup
@@ -436,7 +453,7 @@ def run_ours(args, rank, world, local_rank):
             "GFLOPs": round(e["flops"] / (mean_ms[i] * 1e-3) / 1e9, 1),
             "frac": round(gbs / peak, 3), "err": e["err"], "K": e["info"]["K"],
             "tiles": e["info"]["n_tiles"], "staged_tiles": e["info"]["n_staged_tiles"],
-            "launches": e["info"]["launches_per_exec"],
+            "launches": e["info"]["launches_per_exec"], "tile_shape": e["tile_shape"],
             "moved_over_compulsory": round(e["info"]["moved_bytes"] / e["bytes"], 3),
             "bound_cost": e["cost"]}
     best = {}
@@ -470,9 +487,49 @@ def run_ours(args, rank, world, local_rank):
         "detail": detail,
         "setup_s": round(setup_s, 1),
     }
+    if args.workload == "precision":
+        line["cg_ir"] = precision_solves(S, mats[0], parts_kept, dev, log)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(mats, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+def precision_solves(S, mat, parts, dev, log):
+    """The precision extension: A x = b on the matrix in its DB form (eRCN,
+    K=1024) by CG with FP64 iterative refinement, inner products in FP64,
+    FP32 and BF16 values; b = A x* for a seeded x*.  Reports time to a
+    relative FP64 residual of 1e-10 and the error against x*."""
+    import torch
+    import oracle
+    name, rp, ci, v = mat
+    n = len(rp) - 1
+    kw, _ = form_kwargs(S, "db1024", rp, ci, parts)
+    x_star = synth.uniform_x(n, 7)
+    b, _ = oracle.spmv(n, n, rp, ci, v, x_star)
+    bd = torch.from_numpy(b).to(dev)
+    f64 = S.spmv_plan_create(n, n, rp, ci, v, dtype=S.SPMV_F64, **kw)
+    out = {}
+    for label, dt in (("f64", S.SPMV_F64), ("f32", S.SPMV_F32), ("bf16", S.SPMV_BF16)):
+        low = f64 if dt == S.SPMV_F64 else S.spmv_plan_create(n, n, rp, ci, v, dtype=dt, **kw)
+        xd = torch.zeros(n, dtype=torch.float64, device=dev)
+        S.spmv_cg_ir(low, f64, bd, xd, tol=1e-10)          # warm
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = S.spmv_cg_ir(low, f64, bd, xd, tol=1e-10)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        x = xd.cpu().numpy()
+        ax, _ = oracle.spmv(n, n, rp, ci, v, x)
+        out[label] = {"seconds": round(secs, 4), "outer": info["outer"],
+                      "inner_iterations": info["inner_total"],
+                      "rel_residual_solver": info["rel_residual"],
+                      "rel_residual_oracle": float(np.linalg.norm(b - ax) / np.linalg.norm(b)),
+                      "rel_error_vs_x_star": float(np.linalg.norm(x - x_star)
+                                                   / np.linalg.norm(x_star)),
+                      "converged": info["converged"]}
+        log("  CG-IR %s: %s" % (label, out[label]))
+    return out
 
 
 def main():
@@ -488,6 +545,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="tiled forms with the default tile shape instead of the autotuned one")
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 256, 1024],
+                    help="tiled forms with this CTA shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")
     args = ap.parse_args()

@@ -67,17 +67,21 @@ enum { SPMV_NATURAL = 0, SPMV_SB = 1, SPMV_DB = 2, SPMV_SPLIT = 3 };
 
 /* plan flags */
 enum {
-    SPMV_FLAG_NO_STAGING = 1,    /* never stage x in shared memory (ablation) */
+    SPMV_FLAG_NO_STAGING = 1,    /* never stage x in shared memory (ablation;
+                                    overrides SPMV_FLAG_STAGE) */
     SPMV_FLAG_TILED_NATURAL = 2, /* natural form through the tiled kernel
                                     instead of the plain vector-per-row kernel */
     SPMV_FLAG_SM_AFFINE = 4,     /* persistent CTAs that first work the tiles
                                     queued for their own SM (a part's tiles on
                                     one SM, sharing its L1) (ablation) */
-    SPMV_FLAG_PERSISTENT = 8     /* persistent CTAs, one per resident slot,
+    SPMV_FLAG_PERSISTENT = 8,    /* persistent CTAs, one per resident slot,
                                     claiming tiles in order (ablation); the
                                     default is one CTA per tile, with tiles
                                     sized so that they fill about one wave of
                                     resident CTAs */
+    SPMV_FLAG_STAGE = 16         /* stage x in 256-thread CTAs too; by default
+                                    only wide (1024-thread) CTAs stage, where
+                                    the window is large enough to pay */
 };
 
 /* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,
@@ -130,6 +134,11 @@ typedef struct spmv_opts {
     int32_t lanes;        /* threads cooperating on one row: 2, 4, 8, 16 or 32
                              (0 = chosen from the mean row length) */
     int32_t flags;        /* SPMV_FLAG_* */
+    int32_t cta_threads;  /* tiled forms: 256 = several CTAs per SM, tiles
+                             for one wave of them, x through L1/L2 (0 = this);
+                             1024 = one wide CTA per SM, tiles for four waves,
+                             each staging up to 200 KB of x in shared memory
+                             (for parts with large column windows) */
     /* optional device allocator for plan-owned memory (NULL = cudaMalloc) */
     void *(*alloc)(size_t bytes, void *ctx);
     void (*release)(void *ptr, void *ctx);
@@ -202,6 +211,43 @@ spmv_status spmv_plan_get_info(const spmv_plan *plan, spmv_plan_info *info);
 /* Release the plan and its device memory (synchronises the device first).
  * NULL is accepted. */
 spmv_status spmv_plan_destroy(spmv_plan *plan);
+
+/* Mixed-precision conjugate gradients with iterative refinement (not in the
+ * paper, which computes in FP64, Sec. 5.2): solves A x = b for a symmetric
+ * positive definite A from two plans of it built with the same permutations
+ * and form -- `low` (any dtype) for the inner products and `f64` (SPMV_F64)
+ * for the residual.  Each outer step computes r = b - A x in FP64 with the
+ * f64 plan and stops once ||r||_2 <= tol ||b||_2; otherwise it runs plain CG
+ * on A d = r / ||r|| with the low plan's products (FP32 vectors and
+ * accumulation for F32 / BF16 values, FP64 for F64) until the inner residual
+ * falls by inner_tol, and updates x <- x + ||r|| d in FP64.  The solver works
+ * in the plans' column space (x_hat = x P_c), moving each product from row
+ * to column space when the permutations differ.  Inner iterations run as a
+ * CUDA graph of 8 captured iterations, replayed until the inner test holds.
+ * b, x: n device doubles in the ORIGINAL order; x holds the initial guess on
+ * entry and the solution on return.  Synchronous (work on an internal stream
+ * ordered after `stream`); workspace comes from the low plan's allocator and
+ * is released before returning.
+ * Errors: SPMV_E_INVALID (plans of different shapes / permutations, f64 plan
+ * not SPMV_F64, CG breakdown on a matrix that is not SPD), SPMV_E_UNSUPPORTED
+ * (nrhs != 1), SPMV_E_NOMEM, SPMV_E_CUDA.  Not reaching tol within max_outer
+ * steps is not an error: info->converged is 0. */
+typedef struct spmv_cg_opts {
+    double tol;           /* relative FP64 residual to reach (0 = 1e-10) */
+    double inner_tol;     /* inner relative reduction (0 = 1e-4; 1e-12 for F64) */
+    int32_t max_outer;    /* refinement steps (0 = 50) */
+    int32_t max_inner;    /* inner iterations per step (0 = 2000) */
+} spmv_cg_opts;
+
+typedef struct spmv_cg_info {
+    int32_t outer;        /* refinement steps taken */
+    int32_t inner_total;  /* inner CG iterations, all steps */
+    double rel_residual;  /* ||b - A x||_2 / ||b||_2 in FP64 at return */
+    int32_t converged;    /* rel_residual <= tol */
+} spmv_cg_info;
+
+spmv_status spmv_cg_ir(spmv_plan *low, spmv_plan *f64, const double *b, double *x,
+                       const spmv_cg_opts *opts, spmv_cg_info *info, void *stream);
 
 /* Autotuner (not in the paper; the shapes the paper leaves to OSKI are picked
  * by measurement here): build one plan per candidate option set for the same

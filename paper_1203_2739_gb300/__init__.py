@@ -14,6 +14,7 @@ Function names follow the C ABI:
     spmv_exec             y_hat <- A_hat x_hat (device tensors)
     spmv_exec_host        the same with host buffers (copies inside)
     spmv_plan_check       report a device wait that gave up (SPMV_E_TIMEOUT)
+    spmv_cg_ir            mixed-precision CG with FP64 iterative refinement
     spmv_permute_x / spmv_unpermute_y
     spmv_plan_get_info / spmv_plan_destroy / spmv_last_error
 """
@@ -32,7 +33,7 @@ SPMV_OK, SPMV_E_INVALID, SPMV_E_STRUCTURE, SPMV_E_NOMEM, SPMV_E_CUDA, SPMV_E_TIM
 SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
 SPMV_NATURAL, SPMV_SB, SPMV_DB, SPMV_SPLIT = 0, 1, 2, 3
 SPMV_FLAG_NO_STAGING, SPMV_FLAG_TILED_NATURAL, SPMV_FLAG_SM_AFFINE = 1, 2, 4
-SPMV_FLAG_PERSISTENT = 8
+SPMV_FLAG_PERSISTENT, SPMV_FLAG_STAGE = 8, 16
 SPMV_PART_CN, SPMV_PART_ERCN, SPMV_PART_RCN, SPMV_PART_RANDOM = 0, 1, 2, 3
 SPMV_FIT_CSR, SPMV_FIT_X = 0, 1
 
@@ -46,7 +47,7 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
            "spmv_form_from_labels", "spmv_partition", "spmv_partition_free",
            "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
-           "spmv_plan_check")
+           "spmv_plan_check", "spmv_cg_ir")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
@@ -80,7 +81,8 @@ class spmv_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("tile_nnz", ctypes.c_int32),
                 ("long_row", ctypes.c_int32), ("lanes", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("alloc", _ALLOC_T), ("release", _FREE_T),
+                ("flags", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("alloc", _ALLOC_T), ("release", _FREE_T),
                 ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -112,6 +114,16 @@ class spmv_partition_out(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class spmv_cg_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32)]
+
+
+class spmv_cg_info(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("inner_total", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("converged", ctypes.c_int32)]
+
+
 # ---------------------------------------------------------------- library --
 def _load():
     if not os.path.exists(LIB_PATH):
@@ -125,6 +137,8 @@ def _load():
     L.spmv_exec.argtypes = [vp, vp, vp, vp]
     L.spmv_exec_host.argtypes = [vp, vp, vp, vp]
     L.spmv_plan_check.argtypes = [vp, vp]
+    L.spmv_cg_ir.argtypes = [vp, vp, vp, vp, ctypes.POINTER(spmv_cg_opts),
+                             ctypes.POINTER(spmv_cg_info), vp]
     L.spmv_permute_x.argtypes = [vp, vp, vp, vp]
     L.spmv_unpermute_y.argtypes = [vp, vp, vp, vp]
     L.spmv_plan_get_info.argtypes = [vp, ctypes.POINTER(spmv_plan_info)]
@@ -146,7 +160,7 @@ def _load():
     for name in ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
                  "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
                  "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
-                 "spmv_plan_autotune", "spmv_plan_check"):
+                 "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -237,7 +251,7 @@ class Plan:
 def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
                      form=SPMV_NATURAL, K=0, row_part_ptr=None, col_part_ptr=None,
                      nz_part=None, dtype=SPMV_F64, nrhs=1, tile_cols=0, tile_nnz=0,
-                     long_row=0, lanes=0, flags=0, allocator="torch"):
+                     long_row=0, lanes=0, flags=0, cta_threads=0, allocator="torch"):
     A, keep = _csr_struct(m, n, rowptr, colidx, vals)
     rperm = None if row_perm is None else _i32(row_perm)
     cperm = None if col_perm is None else _i32(col_perm)
@@ -246,7 +260,7 @@ def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
     cpp = None if col_part_ptr is None else _i32(col_part_ptr)
     nzp = None if nz_part is None else _i32(nz_part)
     splits = spmv_splits(form, K, _ptr(rpp), _ptr(cpp), _ptr(nzp))
-    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags)
+    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, cta_threads)
     if allocator == "torch":
         opts.alloc, opts.release = _ALLOC_CB, _FREE_CB
     handle = ctypes.c_void_p()
@@ -274,7 +288,8 @@ def spmv_plan_autotune(m, n, rowptr, colidx, vals, candidates, reps=5, stream=No
     arr = (spmv_opts * len(candidates))()
     for i, c in enumerate(candidates):
         o = arr[i]
-        for k in ("dtype", "nrhs", "tile_cols", "tile_nnz", "long_row", "lanes", "flags"):
+        for k in ("dtype", "nrhs", "tile_cols", "tile_nnz", "long_row", "lanes", "flags",
+                  "cta_threads"):
             setattr(o, k, int(c.get(k, 0)))
         if allocator == "torch":
             o.alloc, o.release = _ALLOC_CB, _FREE_CB
@@ -324,6 +339,28 @@ def spmv_plan_check(plan, stream=None):
     """Synchronise `stream` and raise SpmvError (SPMV_E_TIMEOUT) if a bounded
     device wait of an earlier spmv_exec of the plan gave up."""
     _check(lib.spmv_plan_check(plan.handle, ctypes.c_void_p(_stream_handle(stream))))
+
+
+def spmv_cg_ir(low, f64, b, x, tol=0.0, inner_tol=0.0, max_outer=0, max_inner=0,
+               stream=None):
+    """Solve A x = b (A symmetric positive definite) by CG with iterative
+    refinement: inner products with plan `low`, FP64 residuals with plan
+    `f64` (same matrix and permutations).  b, x: float64 CUDA tensors of n
+    entries in the original order; x is the initial guess and receives the
+    solution.  Returns the solver's info as a dict."""
+    torch = _torch()
+    n = low.info["n"]
+    for t, what in ((b, "b"), (x, "x")):
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("%s must be a contiguous CUDA float64 tensor of %d entries"
+                             % (what, n))
+    o = spmv_cg_opts(tol, inner_tol, max_outer, max_inner)
+    info = spmv_cg_info()
+    _check(lib.spmv_cg_ir(low.handle, f64.handle, ctypes.c_void_p(b.data_ptr()),
+                          ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), ctypes.byref(info),
+                          ctypes.c_void_p(_stream_handle(stream))))
+    return {"outer": info.outer, "inner_total": info.inner_total,
+            "rel_residual": info.rel_residual, "converged": bool(info.converged)}
 
 
 def _host_ptr(a, rows, plan, what):

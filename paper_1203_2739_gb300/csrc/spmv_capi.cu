@@ -6,47 +6,14 @@
 #include <new>
 #include <vector>
 
-#include "spmv_device.h"
+#include "spmv_plan_obj.h"
 
 using namespace spmv;
 
-struct spmv_plan {
-    HostPlan hp;                  // metadata only after upload
-    DevPlan dp;
-    spmv_plan_info info{};
-    void *arena = nullptr;
-    size_t arena_bytes = 0;
-    void *(*alloc)(size_t, void *) = nullptr;
-    void (*release)(void *, void *) = nullptr;
-    void *ctx = nullptr;
-    int device = 0;
-    const int32_t *d_row_perm = nullptr;
-    const int32_t *d_col_perm = nullptr;
-    void *io_x = nullptr, *io_y = nullptr;
-    int32_t *h_status = nullptr;  // pinned copy of the device status word
-    size_t xbytes = 0, ybytes = 0;
-};
-
 namespace {
 
-void *dev_alloc(spmv_plan *p, size_t bytes)
-{
-    if (bytes == 0) bytes = 256;
-    if (p->alloc) return p->alloc(bytes, p->ctx);
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return ptr;
-}
-
-void dev_free(spmv_plan *p, void *ptr)
-{
-    if (!ptr) return;
-    if (p->release) p->release(ptr, p->ctx);
-    else cudaFree(ptr);
-}
+void *dev_alloc(spmv_plan *p, size_t bytes) { return plan_alloc(p, bytes); }
+void dev_free(spmv_plan *p, void *ptr) { plan_free(p, ptr); }
 
 spmv_status cuda_fail(cudaError_t e, const char *what)
 {
@@ -91,6 +58,34 @@ spmv_status device_matches(const spmv_plan *p)
 
 cudaError_t run(const spmv_plan *p, const void *x, void *y, cudaStream_t s)
 {
+    return plan_run(p, x, y, s);
+}
+
+}  // namespace
+
+namespace spmv {
+
+void *plan_alloc(spmv_plan *p, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (p->alloc) return p->alloc(bytes, p->ctx);
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return ptr;
+}
+
+void plan_free(spmv_plan *p, void *ptr)
+{
+    if (!ptr) return;
+    if (p->release) p->release(ptr, p->ctx);
+    else cudaFree(ptr);
+}
+
+cudaError_t plan_run(const spmv_plan *p, const void *x, void *y, cudaStream_t s)
+{
     switch (p->hp.dtype) {
     case SPMV_F64: return exec_f64(p->dp, x, y, s);
     case SPMV_F32: return exec_f32(p->dp, x, y, s);
@@ -98,7 +93,7 @@ cudaError_t run(const spmv_plan *p, const void *x, void *y, cudaStream_t s)
     }
 }
 
-}  // namespace
+}  // namespace spmv
 
 extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm,
                                         const spmv_splits *splits, const spmv_opts *opts,
@@ -243,6 +238,7 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
             }
         }
         a.add(nullptr, sizeof(int32_t), (void **)&dp.status, true);
+        p->same_perm = hp.m == hp.n && hp.row_perm == hp.col_perm;
         if (!hp.row_perm.empty()) add_vec(a, hp.row_perm, (const void **)&p->d_row_perm);
         if (!hp.col_perm.empty()) add_vec(a, hp.col_perm, (const void **)&p->d_col_perm);
 
@@ -286,6 +282,7 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         dp.n_fixups = (int32_t)hp.fixups.size();
         dp.smem_bytes = any_staged ? (hp.max_staged * r * xb + 15) / 16 * 16 : 0;
         dp.nq = nq;
+        dp.cta_threads = hp.cta_threads;
         if (tiled) {
             e = cudaDeviceGetAttribute(&dp.n_sm, cudaDevAttrMultiProcessorCount, p->device);
             if (e != cudaSuccess) {

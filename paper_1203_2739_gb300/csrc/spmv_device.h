@@ -36,6 +36,7 @@ struct DevPlan {
     // persistent schedule (ctr = NULL: one CTA per tile)
     int32_t *ctr = nullptr;            // next-tile counter, finished-CTA counter
     int32_t n_sm = 0;
+    int32_t cta_threads = 256;         // 256, or 1024 (wide: one CTA per SM)
 };
 
 cudaError_t exec_f64(const DevPlan &P, const void *x, void *y, cudaStream_t s);

@@ -67,6 +67,7 @@ struct HostPlan {
     int32_t form = SPMV_NATURAL, K = 0, dtype = SPMV_F64, nrhs = 1;
     int32_t lanes = 8, tile_cols = 0, long_thresh = 0;
     int32_t flags = 0;
+    int32_t cta_threads = 256;     // tiled kernel CTA size (1024: one per SM)
     bool use_k1 = true;            // natural form: vector-per-row kernel
 
     // K1: CSR.  Tiled forms: elements in chunk order, then the long rows.
@@ -99,9 +100,9 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
                             const spmv_splits *splits, const spmv_opts *opts,
                             int32_t n_sm, HostPlan *out);
 
-// Resident CTAs per SM the tiled kernel is sized for (its register budget
-// asks for at least this many).
-constexpr int32_t kTileCtasPerSm = 6;
+// Resident 256-thread CTAs per SM the tiled kernel is sized for (its
+// register budget asks for at least this many), by right-hand-side count.
+inline int32_t tile_ctas_per_sm_for(int32_t r) { return r <= 2 ? 6 : (r == 4 ? 4 : 3); }
 
 // Round-to-nearest-even FP64 -> BF16 bits.
 uint16_t bf16_rne(double v);

@@ -38,6 +38,7 @@
 namespace spmv {
 
 constexpr int kThreads = 256;
+constexpr int kWideThreads = 1024;
 
 // Tuning knobs (compile-time):
 //   SPMV_STREAM_HINT  how the matrix stream (values, indices) is loaded:
@@ -51,11 +52,12 @@ constexpr int kThreads = 256;
 #ifndef SPMV_TILE_MINBLOCKS
 #define SPMV_TILE_MINBLOCKS 6
 #endif
-//   SPMV_CHUNK_PAIR   1 = a warp works on two chunks of 32 rows at once
-//                     (single right-hand side)
-#ifndef SPMV_CHUNK_PAIR
-#define SPMV_CHUNK_PAIR 0
-#endif
+// resident 256-thread tile CTAs per SM the register budget is sized for:
+// fewer for many right-hand sides, which hold r accumulators per lane
+constexpr int tile_ctas_per_sm(int r)
+{
+    return r <= 2 ? SPMV_TILE_MINBLOCKS : (r == 4 ? 4 : 3);
+}
 
 // loads of the matrix stream, read exactly once per SpMV
 __device__ __forceinline__ double ld_stream(const double *p)
@@ -125,10 +127,10 @@ __device__ __forceinline__ T group_sum(T v)
 
 // Sum s[] over the CTA; the result is valid in thread 0.  Every thread of the
 // CTA must call it.
-template <int R, typename T>
+template <int R, typename T, int NT = kThreads>
 __device__ __forceinline__ void block_sum(T (&s)[R])
 {
-    __shared__ T red[R][kThreads / 32];
+    __shared__ T red[R][NT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < R; ++c) {
@@ -139,7 +141,7 @@ __device__ __forceinline__ void block_sum(T (&s)[R])
     if (warp == 0) {
 #pragma unroll
         for (int c = 0; c < R; ++c) {
-            T v = lane < kThreads / 32 ? red[c][lane] : T(0);
+            T v = lane < NT / 32 ? red[c][lane] : T(0);
             s[c] = group_sum<32>(v);
         }
     }
@@ -265,10 +267,157 @@ struct TileArgs {
 // i of the chunk and runs one FMA chain over its row: element k of the
 // chunk's rows sits at chunk_off + 32 k + i, so every load is coalesced and
 // every FP64 FMA runs with the lanes of all rows still going.
+// The x entries of one stored element for all right-hand sides.  NARROW:
+// staged; GLOBAL: gathered from L2; MIXED (ci < 0: gathered entry ~ci):
+// both loads are issued -- the unused one reads entry 0 -- and one is
+// selected, so the gathers of a batch carry no branch and are all in flight
+// together.
+template <int KIND, int R, typename XT>
+__device__ __forceinline__ void fetch_x(int32_t ci, const XT *seg, const XT *__restrict__ x,
+                                        XT (&o)[R])
+{
+    if (KIND == TILE_NARROW) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) o[c] = seg[ci * R + c];
+    } else if (KIND == TILE_GLOBAL) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) o[c] = __ldg(x + (int64_t)ci * R + c);
+    } else {
+        const bool g = ci < 0;
+        const int64_t gi = g ? (int64_t)(~ci) : 0;
+        const int32_t si = g ? 0 : ci;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            const XT a = __ldg(x + gi * R + c);
+            const XT b = seg[si * R + c];
+            o[c] = g ? a : b;
+        }
+    }
+}
+
+// The rows of a tile after staging, for one tile kind.  Loads are issued for
+// every slot of a batch (slots past a row's end read element 0 of the
+// chunk, a valid address) and the FMAs of those slots are discarded by a
+// select, so a batch has no branches.
+template <int KIND, int R, typename VT, typename XT, int NT>
+__device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> &A,
+                                          const XT *seg)
+{
+    const int32_t *__restrict__ chunk_off = A.chunk_off;
+    const int32_t *__restrict__ slot_dst = A.slot_dst;
+    const int32_t *__restrict__ slot_len = A.slot_len;
+    const VRow *__restrict__ vrows = A.vrows;
+    const uint16_t *__restrict__ c16 = A.c16;
+    const int32_t *__restrict__ c32 = A.c32;
+    const VT *__restrict__ val = A.val;
+    const XT *__restrict__ x = A.x;
+    XT *__restrict__ y = A.y;
+    XT *__restrict__ partial = A.partial;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto colat = [&](int64_t e) -> int32_t {
+        return KIND == TILE_NARROW ? (int32_t)ld_stream(c16 + e) : ld_stream(c32 + e);
+    };
+    auto store = [&](int32_t d, const XT (&s)[R]) {
+        if (d >= 0) {
+#pragma unroll
+            for (int c = 0; c < R; ++c) y[(int64_t)d * R + c] = s[c];
+        } else if (d <= -2) {
+            const int64_t ps = (int64_t)(-d - 2) * R;
+#pragma unroll
+            for (int c = 0; c < R; ++c) partial[ps + c] = s[c];
+        }
+    };
+    constexpr int U = R == 1 ? 8 : (R == 2 ? 4 : 2);
+
+    // rows too long for one lane: a warp each, batches of U loads per lane
+    for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += NT / 32) {
+        const VRow row = vrows[vr];
+        XT s[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) s[c] = XT(0);
+        for (int32_t k0 = 0; k0 < row.len; k0 += 32 * U) {
+            XT v[U];
+            int32_t ci[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t k = k0 + u * 32 + lane;
+                const int64_t e = row.e0 + (k < row.len ? k : 0);
+                v[u] = (XT)load_val(val + e);
+                ci[u] = colat(e);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                XT xo[R];
+                fetch_x<KIND, R, XT>(ci[u], seg, x, xo);
+                const bool on = k0 + u * 32 + lane < row.len;
+#pragma unroll
+                for (int c = 0; c < R; ++c) {
+                    const XT f = fma(v[u], xo[c], s[c]);
+                    s[c] = on ? f : s[c];
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < R; ++c) s[c] = group_sum<32>(s[c]);
+        if (lane == 0) store(row.dst, s);
+    }
+
+    // chunks of 32 rows, one lane per row, batches of U elements per lane.
+    // A chunk's metadata (row length, destination, offset) is loaded one
+    // chunk ahead, so a chunk costs two dependent trips to memory (its
+    // stream, then its gathers) instead of four.
+    const int32_t cend = t.chunk0 + t.nchunks;
+    int32_t ch = t.chunk0 + warp;
+    int32_t len_n = 0, dst_n = -1, off_n = 0;
+    if (ch < cend) {
+        len_n = __ldg(slot_len + ch * 32 + lane);
+        dst_n = __ldg(slot_dst + ch * 32 + lane);
+        off_n = __ldg(chunk_off + ch);
+    }
+    for (; ch < cend; ch += NT / 32) {
+        const int32_t len = len_n, dst = dst_n;
+        const int64_t off = (int64_t)off_n + lane;
+        const int32_t chn = ch + NT / 32;
+        if (chn < cend) {
+            len_n = __ldg(slot_len + chn * 32 + lane);
+            dst_n = __ldg(slot_dst + chn * 32 + lane);
+            off_n = __ldg(chunk_off + chn);
+        }
+        const int32_t L = __shfl_sync(0xffffffffu, len, 0);   // rows sorted: lane 0 is longest
+        XT s[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) s[c] = XT(0);
+        for (int32_t k0 = 0; k0 < L; k0 += U) {
+            XT v[U];
+            int32_t ci[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                // slots past the row's end (or past the chunk's longest row)
+                // read the chunk's first element
+                const int64_t e = off + (k0 + u < L ? (int64_t)(k0 + u) * 32 : 0);
+                v[u] = (XT)load_val(val + e);
+                ci[u] = colat(e);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                XT xo[R];
+                fetch_x<KIND, R, XT>(ci[u], seg, x, xo);
+                const bool on = k0 + u < len;
+#pragma unroll
+                for (int c = 0; c < R; ++c) {
+                    const XT f = fma(v[u], xo[c], s[c]);
+                    s[c] = on ? f : s[c];
+                }
+            }
+        }
+        store(dst, s);
+    }
+}
+
 // Returns false when the staging copy did not complete within the wait limit
 // (the tile is then skipped and A.status raised).  `bar` is the CTA's
 // mbarrier, `phase` its current parity.
-template <int R, typename VT, typename XT>
+template <int R, typename VT, typename XT, int NT = kThreads>
 __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> &A,
                                           uint64_t *bar, uint32_t &phase)
 {
@@ -290,13 +439,13 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
         XT s[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) s[c] = XT(0);
-        for (int32_t e = t.e0 + (int32_t)threadIdx.x; e < t.e1; e += kThreads) {
+        for (int32_t e = t.e0 + (int32_t)threadIdx.x; e < t.e1; e += NT) {
             const XT v = (XT)load_val(val + e);
             const int64_t xc = (int64_t)ld_stream(c32 + e) * R;
 #pragma unroll
             for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
         }
-        block_sum<R>(s);
+        block_sum<R, XT, NT>(s);
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int c = 0; c < R; ++c) partial[(int64_t)t.slot * R + c] = s[c];
@@ -313,16 +462,16 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
         const uint32_t body = (uint32_t)(run_elems * (int32_t)sizeof(XT)) & ~15u;
         if (threadIdx.x == 0 && body > 0)
             bulk_copy_g2s(seg, x + (int64_t)t.run0 * R, body, bar);
-        for (int32_t i = (int32_t)(body / sizeof(XT)) + threadIdx.x; i < run_elems; i += kThreads)
+        for (int32_t i = (int32_t)(body / sizeof(XT)) + threadIdx.x; i < run_elems; i += NT)
             seg[i] = __ldg(x + (int64_t)t.run0 * R + i);
         // list: batches of 8 entries per thread, every index load issued
         // before the gathers that depend on them
         constexpr int LB = R == 1 ? 8 : (R == 2 ? 4 : (R == 4 ? 2 : 1));
-        for (int32_t i0 = 0; i0 < t.listlen; i0 += LB * kThreads) {
+        for (int32_t i0 = 0; i0 < t.listlen; i0 += LB * NT) {
             int32_t src[LB];
 #pragma unroll
             for (int u = 0; u < LB; ++u) {
-                const int32_t i = i0 + u * kThreads + (int32_t)threadIdx.x;
+                const int32_t i = i0 + u * NT + (int32_t)threadIdx.x;
                 src[u] = i < t.listlen ? __ldg(xlist + t.list0 + i) : -1;
             }
             XT v[LB][R];
@@ -333,7 +482,7 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
                     v[u][c] = src[u] >= 0 ? __ldg(x + (int64_t)src[u] * R + c) : XT(0);
 #pragma unroll
             for (int u = 0; u < LB; ++u) {
-                const int32_t i = i0 + u * kThreads + (int32_t)threadIdx.x;
+                const int32_t i = i0 + u * NT + (int32_t)threadIdx.x;
                 if (i < t.listlen) {
 #pragma unroll
                     for (int c = 0; c < R; ++c) seg[(t.runlen + i) * R + c] = v[u][c];
@@ -355,148 +504,18 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
         }
     }
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the x entry of element e for right-hand side c
-    auto xat = [&](int32_t ci, int c) -> XT {
-        if (kind == TILE_GLOBAL) return __ldg(x + (int64_t)ci * R + c);
-        if (ci >= 0) return seg[ci * R + c];
-        return __ldg(x + (int64_t)(~ci) * R + c);
-    };
-    auto colat = [&](int64_t e) -> int32_t {
-        return kind == TILE_NARROW ? (int32_t)ld_stream(c16 + e) : ld_stream(c32 + e);
-    };
-    auto store = [&](int32_t d, const XT (&s)[R]) {
-        if (d >= 0) {
-#pragma unroll
-            for (int c = 0; c < R; ++c) y[(int64_t)d * R + c] = s[c];
-        } else if (d <= -2) {
-            const int64_t ps = (int64_t)(-d - 2) * R;
-#pragma unroll
-            for (int c = 0; c < R; ++c) partial[ps + c] = s[c];
-        }
-    };
-    constexpr int U = R == 1 ? 8 : (R == 2 ? 4 : 2);
-
-    // rows too long for one lane: a warp each, batches of U loads per lane
-    for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += kThreads / 32) {
-        const VRow row = vrows[vr];
-        XT s[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = XT(0);
-        for (int32_t k0 = 0; k0 < row.len; k0 += 32 * U) {
-            XT v[U];
-            int32_t ci[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int32_t k = k0 + u * 32 + lane;
-                const bool on = k < row.len;
-                v[u] = on ? (XT)load_val(val + row.e0 + k) : XT(0);
-                ci[u] = on ? colat(row.e0 + k) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (k0 + u * 32 + lane < row.len) {
-#pragma unroll
-                    for (int c = 0; c < R; ++c) s[c] = fma(v[u], xat(ci[u], c), s[c]);
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = group_sum<32>(s[c]);
-        if (lane == 0) store(row.dst, s);
-    }
-
-#if SPMV_CHUNK_PAIR
-    if (R == 1) {
-        // two neighbouring chunks per warp at a time: twice the independent
-        // loads and gathers in flight per lane
-        constexpr int UP = 4;
-        const int32_t cend = t.chunk0 + t.nchunks;
-        for (int32_t ch = t.chunk0 + 2 * warp; ch < cend; ch += 2 * (kThreads / 32)) {
-            const bool hasb = ch + 1 < cend;
-            const int32_t slota = ch * 32 + lane, slotb = slota + 32;
-            const int32_t lena = __ldg(slot_len + slota);
-            const int32_t lenb = hasb ? __ldg(slot_len + slotb) : 0;
-            const int64_t offa = __ldg(chunk_off + ch) + lane;
-            const int64_t offb = hasb ? __ldg(chunk_off + ch + 1) + lane : 0;
-            const int32_t L = __shfl_sync(0xffffffffu, max(lena, lenb), 0);
-            XT sa[R] = {XT(0)}, sb[R] = {XT(0)};
-            for (int32_t k0 = 0; k0 < L; k0 += UP) {
-                XT va[UP], vb[UP];
-                int32_t ca[UP], cb[UP];
-#pragma unroll
-                for (int u = 0; u < UP; ++u) {
-                    const bool ona = k0 + u < lena, onb = k0 + u < lenb;
-                    const int64_t ea = offa + (int64_t)(k0 + u) * 32;
-                    const int64_t eb = offb + (int64_t)(k0 + u) * 32;
-                    va[u] = ona ? (XT)load_val(val + ea) : XT(0);
-                    ca[u] = ona ? colat(ea) : 0;
-                    vb[u] = onb ? (XT)load_val(val + eb) : XT(0);
-                    cb[u] = onb ? colat(eb) : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < UP; ++u) {
-                    if (k0 + u < lena) sa[0] = fma(va[u], xat(ca[u], 0), sa[0]);
-                    if (k0 + u < lenb) sb[0] = fma(vb[u], xat(cb[u], 0), sb[0]);
-                }
-            }
-            store(__ldg(slot_dst + slota), sa);
-            if (hasb) store(__ldg(slot_dst + slotb), sb);
-        }
-        return true;
-    }
-#endif
-    // chunks of 32 rows, one lane per row, batches of U elements per lane.
-    // A chunk's metadata (row length, destination, offset) is loaded one
-    // chunk ahead, so a chunk costs two dependent trips to memory (its
-    // stream, then its gathers) instead of four.
-    const int32_t cend = t.chunk0 + t.nchunks;
-    int32_t ch = t.chunk0 + warp;
-    int32_t len_n = 0, dst_n = -1, off_n = 0;
-    if (ch < cend) {
-        len_n = __ldg(slot_len + ch * 32 + lane);
-        dst_n = __ldg(slot_dst + ch * 32 + lane);
-        off_n = __ldg(chunk_off + ch);
-    }
-    for (; ch < cend; ch += kThreads / 32) {
-        const int32_t len = len_n, dst = dst_n;
-        const int64_t off = (int64_t)off_n + lane;
-        const int32_t chn = ch + kThreads / 32;
-        if (chn < cend) {
-            len_n = __ldg(slot_len + chn * 32 + lane);
-            dst_n = __ldg(slot_dst + chn * 32 + lane);
-            off_n = __ldg(chunk_off + chn);
-        }
-        const int32_t L = __shfl_sync(0xffffffffu, len, 0);   // rows sorted: lane 0 is longest
-        XT s[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = XT(0);
-        for (int32_t k0 = 0; k0 < L; k0 += U) {
-            XT v[U];
-            int32_t ci[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool on = k0 + u < len;
-                const int64_t e = off + (int64_t)(k0 + u) * 32;
-                v[u] = on ? (XT)load_val(val + e) : XT(0);
-                ci[u] = on ? colat(e) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (k0 + u < len) {
-#pragma unroll
-                    for (int c = 0; c < R; ++c) s[c] = fma(v[u], xat(ci[u], c), s[c]);
-                }
-            }
-        }
-        store(dst, s);
+    switch (kind) {
+    case TILE_NARROW: rows_work<TILE_NARROW, R, VT, XT, NT>(t, A, seg); break;
+    case TILE_MIXED: rows_work<TILE_MIXED, R, VT, XT, NT>(t, A, seg); break;
+    default: rows_work<TILE_GLOBAL, R, VT, XT, NT>(t, A, seg); break;
     }
     return true;
 }
 
-// One CTA per tile, in tile order.
-template <int R, typename VT, typename XT>
-__global__ void __launch_bounds__(kThreads, SPMV_TILE_MINBLOCKS)
+// One CTA per tile, in tile order.  NT = kThreads: several CTAs per SM;
+// NT = kWideThreads: one wide CTA per SM with a large staging window.
+template <int R, typename VT, typename XT, int NT>
+__global__ void __launch_bounds__(NT, NT == kThreads ? tile_ctas_per_sm(R) : 1)
 k_tiles(const TileArgs<VT, XT> A)
 {
     __shared__ __align__(8) uint64_t bar;
@@ -504,7 +523,7 @@ k_tiles(const TileArgs<VT, XT> A)
     __syncthreads();
     uint32_t phase = 0;
     const Tile t = A.tiles[blockIdx.x];
-    tile_work<R, VT, XT>(t, A, &bar, phase);
+    tile_work<R, VT, XT, NT>(t, A, &bar, phase);
 }
 
 // Persistent CTAs, one per resident slot, claiming tiles in tile order from
@@ -758,8 +777,13 @@ cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
             const int64_t grid = std::min<int64_t>((int64_t)P.n_sm * std::max(per_sm, 1),
                                                    (int64_t)P.n_tiles);
             kern<<<(unsigned)grid, kThreads, P.smem_bytes, s>>>(A, P.n_tiles, P.ctr);
+        } else if (P.cta_threads == kWideThreads) {
+            auto kern = k_tiles<R, VT, XT, kWideThreads>;
+            e = ensure_smem(kern, P.smem_bytes);
+            if (e != cudaSuccess) return e;
+            kern<<<(unsigned)P.n_tiles, kWideThreads, P.smem_bytes, s>>>(A);
         } else {
-            auto kern = k_tiles<R, VT, XT>;
+            auto kern = k_tiles<R, VT, XT, kThreads>;
             e = ensure_smem(kern, P.smem_bytes);
             if (e != cudaSuccess) return e;
             kern<<<(unsigned)P.n_tiles, kThreads, P.smem_bytes, s>>>(A);

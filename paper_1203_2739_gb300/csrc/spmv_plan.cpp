@@ -494,9 +494,23 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     const int64_t nnz = A->nnz;
     const int xb = (o.dtype == SPMV_F64) ? 8 : 4;
     const int r = o.nrhs;
-    // shared memory of a CTA: the staged x entries (default: 36 KB, so that
-    // kTileCtasPerSm CTAs fit an SM's 228 KB next to some L1)
-    int32_t W = o.tile_cols > 0 ? o.tile_cols : (36 * 1024) / (xb * r);
+    // CTA shape: 6 CTAs of 256 threads per SM (fewer for 4 or 8 right-hand
+    // sides), each staging up to 36 KB of x (they fit an SM's 228 KB next to some L1), or one wide
+    // CTA of 1024 threads per SM staging up to 200 KB
+    if (o.cta_threads != 0 && o.cta_threads != 256 && o.cta_threads != 1024) {
+        set_error("cta_threads=%d: must be 0, 256 or 1024", o.cta_threads);
+        return SPMV_E_INVALID;
+    }
+    const bool wide = o.cta_threads == 1024;
+    if (wide && (o.flags & (SPMV_FLAG_SM_AFFINE | SPMV_FLAG_PERSISTENT))) {
+        set_error("cta_threads=1024 runs one CTA per tile (no persistent or SM-affine launch)");
+        return SPMV_E_INVALID;
+    }
+    // tiles per SM of a launch: one wave of the 256-thread CTAs; four waves
+    // of wide CTAs (one per SM), so a slow tile does not hold up an SM
+    const int32_t ctas_per_sm = wide ? 4 : tile_ctas_per_sm_for(r);
+    int32_t W = o.tile_cols > 0 ? o.tile_cols
+                                : std::min<int32_t>(65535, ((wide ? 200 : 36) * 1024) / (xb * r));
     if ((int64_t)W * xb * r > 220 * 1024 || W > 65535) {
         set_error("tile_cols=%d does not fit shared memory (x entries of %d bytes, r=%d)", W,
                   xb, r);
@@ -509,7 +523,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     P->dtype = o.dtype;
     P->nrhs = r;
     if (o.flags & ~(SPMV_FLAG_NO_STAGING | SPMV_FLAG_TILED_NATURAL | SPMV_FLAG_SM_AFFINE |
-                    SPMV_FLAG_PERSISTENT)) {
+                    SPMV_FLAG_PERSISTENT | SPMV_FLAG_STAGE)) {
         set_error("unknown flag bits 0x%x", o.flags);
         return SPMV_E_INVALID;
     }
@@ -518,6 +532,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         return SPMV_E_INVALID;
     }
     P->flags = o.flags;
+    P->cta_threads = o.cta_threads == 1024 ? 1024 : 256;
     P->tile_cols = W;
 
     // permutation
@@ -673,19 +688,19 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     cfg.max_rows = 4096;
     cfg.vrow_len = 64;
     // tiles sized so that one launch is about one wave of resident CTAs
-    // (kTileCtasPerSm per SM): every CTA starts at once and none waits for
+    // (ctas_per_sm per SM): every CTA starts at once and none waits for
     // a slot, so there is no tail wave.  Rows longer than long_t are cut into
     // chunk tiles of the same budget (at least 4096 nonzeros); the fix-up
     // kernel adds their pieces.
     {
-        const int64_t slots = (int64_t)(n_sm > 0 ? n_sm : 152) * kTileCtasPerSm;
+        const int64_t slots = (int64_t)(n_sm > 0 ? n_sm : 152) * ctas_per_sm;
         const int64_t want = std::max<int64_t>((nnz + slots - 1) / slots, 1024);
         cfg.tnnz = o.tile_nnz > 0 ? o.tile_nnz : (int32_t)std::min<int64_t>(want, 1 << 26);
         cfg.chunk = std::max<int32_t>(4096, cfg.tnnz);
         // rows up to a quarter of a tile stay in the tiles (a warp each)
         cfg.long_t = o.long_row > 0 ? o.long_row : std::max<int32_t>(1024, cfg.tnnz / 4);
     }
-    cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING);
+    cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING) && (wide || (o.flags & SPMV_FLAG_STAGE));
     P->lanes = 32;                 // one lane per row, 32 rows per chunk
     P->long_thresh = cfg.long_t;
 

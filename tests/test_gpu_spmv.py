@@ -104,12 +104,18 @@ def test_sb_mesh_exact_and_staged(K):
     lab = _contiguous_labels(m, K)
     rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SB, K, lab)
     plan = S.spmv_plan_create(m, n, rp, ci, vi, row_perm=rperm, col_perm=cperm, form=S.SPMV_SB,
-                              K=K, row_part_ptr=rpp, col_part_ptr=cpp, tile_cols=1024)
+                              K=K, row_part_ptr=rpp, col_part_ptr=cpp, tile_cols=1024,
+                              flags=S.SPMV_FLAG_STAGE)
     assert plan.info["n_staged_tiles"] > 0
     for dtype in (0, 1, 2):
         p = S.spmv_plan_create(m, n, rp, ci, vi, row_perm=rperm, col_perm=cperm,
                                form=S.SPMV_SB, K=K, row_part_ptr=rpp, col_part_ptr=cpp,
-                               tile_cols=1024, dtype=dtype)
+                               tile_cols=1024, dtype=dtype, flags=S.SPMV_FLAG_STAGE)
+        _check(p, m, n, rp, ci, vi, synth.integer_x(n, 3), exact=True)
+        p = S.spmv_plan_create(m, n, rp, ci, vi, row_perm=rperm, col_perm=cperm,
+                               form=S.SPMV_SB, K=K, row_part_ptr=rpp, col_part_ptr=cpp,
+                               dtype=dtype)
+        assert p.info["n_staged_tiles"] == 0      # default: 256-thread CTAs stage nothing
         _check(p, m, n, rp, ci, vi, synth.integer_x(n, 3), exact=True)
 
 
@@ -160,7 +166,8 @@ def _mesh_sb(nx, K, seed=0):
 def test_staged_runs_exact(nx, dtype, nrhs):
     m, n, rp, ci, kw = _mesh_sb(nx, 16)
     vi = synth.integer_values(int(rp[-1]), 21)
-    plan = S.spmv_plan_create(m, n, rp, ci, vi, dtype=dtype, nrhs=nrhs, tile_nnz=2048, **kw)
+    plan = S.spmv_plan_create(m, n, rp, ci, vi, dtype=dtype, nrhs=nrhs, tile_nnz=2048,
+                              flags=S.SPMV_FLAG_STAGE, **kw)
     assert plan.info["n_staged_tiles"] > 0
     assert plan.info["smem_bytes"] % 16 == 0
     x = synth.integer_x(n, 22, nrhs=nrhs)
@@ -173,10 +180,47 @@ def test_staged_runs_persistent_repeat(flags):
     # alternates) and reset their claim counters for the next launch
     m, n, rp, ci, kw = _mesh_sb(96, 64)
     vi = synth.integer_values(int(rp[-1]), 23)
-    plan = S.spmv_plan_create(m, n, rp, ci, vi, tile_nnz=2048, flags=flags, **kw)
+    plan = S.spmv_plan_create(m, n, rp, ci, vi, tile_nnz=2048, flags=flags | S.SPMV_FLAG_STAGE,
+                              **kw)
     assert plan.info["n_staged_tiles"] > 1
     for seed in (24, 25, 26):
         _check(plan, m, n, rp, ci, vi, synth.integer_x(n, seed), exact=True)
+
+
+@pytest.mark.parametrize("nrhs", [1, 8])
+@pytest.mark.parametrize("dtype", [0, 2])
+def test_wide_ctas_exact(zipf, dtype, nrhs):
+    # one 1024-thread CTA per tile with a large staging window
+    m, n, rp, ci, _ = zipf
+    vi = synth.integer_values(int(rp[-1]), 31)
+    x = synth.integer_x(n, 32, nrhs=nrhs)
+    for plan in (_sb_plan(m, n, rp, ci, vi, 8, 33, dtype=dtype, nrhs=nrhs, cta_threads=1024),
+                 _split_plan(m, n, rp, ci, vi, 16, 34, dtype=dtype, nrhs=nrhs, cta_threads=1024,
+                             tile_nnz=8192),
+                 S.spmv_plan_create(m, n, rp, ci, vi, dtype=dtype, nrhs=nrhs, cta_threads=1024,
+                                    flags=S.SPMV_FLAG_TILED_NATURAL, long_row=200)):
+        _check(plan, m, n, rp, ci, vi, x, exact=True)
+
+
+def test_wide_ctas_staged_mesh():
+    m, n, rp, ci, kw = _mesh_sb(96, 16)
+    vi = synth.integer_values(int(rp[-1]), 35)
+    plan = S.spmv_plan_create(m, n, rp, ci, vi, cta_threads=1024, tile_nnz=16384, **kw)
+    assert plan.info["n_staged_tiles"] > 0
+    _check(plan, m, n, rp, ci, vi, synth.integer_x(n, 36), exact=True)
+
+
+def test_autotune_keeps_a_correct_plan(zipf):
+    m, n, rp, ci, _ = zipf
+    vi = synth.integer_values(int(rp[-1]), 41)
+    lab = synth.random_labels(m, 8, 42)
+    rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SB, 8, lab)
+    cands = [dict(), dict(cta_threads=1024), dict(flags=S.SPMV_FLAG_STAGE, tile_nnz=4096)]
+    plan, best, ms = S.spmv_plan_autotune(m, n, rp, ci, vi, cands, reps=3, row_perm=rperm,
+                                          col_perm=cperm, form=S.SPMV_SB, K=8,
+                                          row_part_ptr=rpp, col_part_ptr=cpp)
+    assert 0 <= best < len(cands) and ms > 0
+    _check(plan, m, n, rp, ci, vi, synth.integer_x(n, 43), exact=True)
 
 
 def test_misaligned_x_rejected(zipf):
