@@ -46,12 +46,28 @@ MATRICES = {
               ("blocks64_0.2pct", lambda: synth.blocks(seed=0))],
     "zipf16k": [("zipf16k", lambda: synth.zipf_matrix(seed=0))],
     "precision": [("laplace3d_128", lambda: synth.laplacian3d(128, seed=0))],
+    "scale": [("mesh5_6144", lambda: synth.mesh5(6144, seed=0))],
+    "batching": [("rmat_batch64", lambda: _batch_matrix("rmat_batch64"))],
 }
+BATCHES = {}
+
+
+def _batch_matrix(name):
+    """The batch as one block-diagonal CSR (the natural-form baseline runs it
+    as one matrix); the member matrices are kept for the batched plan."""
+    mats = synth.rmat_batch(64, seed=0)
+    BATCHES[name] = mats
+    return synth.block_diagonal(mats)
 WORKLOAD_TEXT = {
     "sweep": "FP64 reordering sweep: mesh 1024^2 (5-pt, permuted), R-MAT 2^20 deg 16, "
              "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random, SB K=1024, "
              "DB K=1024, split K=4/16/64/256",
     "zipf16k": "Zipf 16384^2 (rows P(d)~d^-1.7498 on [1,512], Zipf(1.2) columns), natural vs SB",
+    "batching": "64 R-MAT matrices (rows log-uniform in [1024, 65536], power-of-two sizes, "
+                "degree U[8,32]) in one plan: natural block-diagonal vs batched split K=16 "
+                "(row-column-net bisection of each matrix); FP32 with --dtype f32",
+    "scale": "L2-exceeding point: 5-pt mesh 6144^2 (37.7M rows, 188.7M nnz, x = 302 MB), "
+             "permuted; natural vs SB K=1024",
     "precision": "7-pt Dirichlet Laplacian 128^3, permuted; natural, random, DB K=1024 "
                  "SpMV in the chosen dtype; CG with FP64 iterative refinement to 1e-10 "
                  "with FP64 / FP32 / BF16 inner products",
@@ -128,10 +144,22 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     return res
 
 
+def batched_split_plan(S, mats, K, dtype, threads):
+    """One plan over a batch of matrices, each split K ways by its own
+    row-column-net bisection (Sec. 4.1)."""
+    def labels(mat):
+        m, n, rp, ci, _ = mat
+        return S.spmv_partition(m, n, rp, ci, S.SPMV_PART_RCN, K=K, seed=0,
+                                threads=1)["labels"]
+    with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        nz = list(ex.map(labels, mats))
+    return S.spmv_plan_create_batched(mats, nz_parts=nz, K=K, dtype=dtype)
+
+
 def form_kwargs(S, f, rp, ci, parts, seed=0):
     """spmv_plan_create arguments of a form, and the partition it came from."""
     m = n = len(rp) - 1
-    if f == "natural":
+    if f == "natural" or f.startswith("batch"):
         return {}, None
     if f == "tiled":
         return dict(flags=S.SPMV_FLAG_TILED_NATURAL), None
@@ -221,6 +249,17 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def kernel_name(info, dtype):
+    """The kernel a plan's exec launches (the fix-up aside), as ncu names it."""
+    vt, xt = {"f64": ("double", "double"), "f32": ("float", "float"),
+              "bf16": ("__nv_bfloat16", "float")}[dtype]
+    r = info["nrhs"]
+    if info["n_tiles"] == 0:
+        return "k_csr_vector<%d, %d, %s, %s>" % (info["lanes"], r, vt, xt)
+    nt = 1024 if info.get("cta_threads", 256) == 1024 else 256
+    return "k_tiles<%d, %s, %s, %d>" % (r, vt, xt, nt)
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1203_2739_gb300", "csrc")
@@ -231,9 +270,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(label):
-    """DRAM bytes per launch recorded from an ncu capture of the current kernel
-    sources (profiles/ncu_traffic.json); None when absent or stale."""
+def ncu_traffic(label, kernel):
+    """DRAM bytes per launch of `kernel` on plan `label` recorded from an ncu
+    capture of the current kernel sources (profiles/ncu_traffic.json, keyed
+    "label kernel"); None when absent or stale."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -242,7 +282,7 @@ def ncu_traffic(label):
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    e = d.get("entries", {}).get(label)
+    e = d.get("entries", {}).get("%s %s" % (label, kernel))
     return None if e is None else e.get("dram_bytes_per_launch")
 
 
@@ -321,6 +361,8 @@ def run_ours(args, rank, world, local_rank):
     forms = args.forms.split(",") if args.forms else (
         FORMS_SWEEP if args.workload == "sweep" else (
             ["natural", "random", "db1024"] if args.workload == "precision"
+            else ["natural", "sb1024"] if args.workload == "scale"
+            else ["natural", "batch_split16"] if args.workload == "batching"
             else ["natural", "sb8", "split16"]))
     dtype = {"f64": S.SPMV_F64, "f32": S.SPMV_F32, "bf16": S.SPMV_BF16}[args.dtype]
     vb, xb = {0: (8, 8), 1: (4, 4), 2: (2, 4)}[dtype]
@@ -349,17 +391,24 @@ def run_ours(args, rank, world, local_rank):
             kw, pres = form_kwargs(S, f, rp, ci, parts)
             t1 = time.perf_counter()
             chosen = None
-            if f in ("natural", "random") or args.no_autotune:
+            # tile shapes: one wave of 256-thread tiles, wide tiles, or eight
+            # waves of smaller tiles (launched in order, so that the x windows
+            # of the tiles running at once stay within L2 when x does not)
+            shapes = {"cta256": dict(dtype=dtype), "cta1024": dict(dtype=dtype, cta_threads=1024),
+                      "cta256x8": dict(dtype=dtype,
+                                       tile_nnz=max(1024, int(rp[-1]) // (8 * 912)))}
+            if f.startswith("batch_split"):
+                plan = batched_split_plan(S, BATCHES[name], int(f[11:]), dtype, threads)
+            elif f in ("natural", "random") or args.no_autotune:
                 plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, **kw)
-            elif args.cta_threads:
-                plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype,
-                                          cta_threads=args.cta_threads, **kw)
-                chosen = "cta%d" % args.cta_threads
+            elif args.shape:
+                plan = S.spmv_plan_create(m, n, rp, ci, v, **shapes[args.shape], **kw)
+                chosen = args.shape
             else:
-                # the tile shape is picked by measurement among the candidates
-                cands = [dict(dtype=dtype), dict(dtype=dtype, cta_threads=1024)]
-                plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v, cands, reps=5, **kw)
-                chosen = "cta1024" if cands[ibest].get("cta_threads") else "cta256"
+                names = list(shapes)
+                plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v,
+                                                      [shapes[k] for k in names], reps=5, **kw)
+                chosen = names[ibest]
             xh = torch.empty_like(xt)
             S.spmv_permute_x(plan, xt, xh)
             yh = torch.empty(m, dtype=tdt, device=dev)
@@ -442,9 +491,24 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
-    dom = int(np.argmax(mean_ms))
-    d = entries[dom]
-    achieved = d["bytes"] / (mean_ms[dom] * 1e-3) / 1e9
+    # the dominant kernel: the kernel instance with the largest share of the
+    # step's device time (plans launching the same kernel grouped); its
+    # achieved bandwidth is the algorithmic bytes of its launches over their
+    # summed duration
+    groups = {}
+    for i, e in enumerate(entries):
+        groups.setdefault(kernel_name(e["info"], args.dtype), []).append(i)
+    dom_kernel = max(groups, key=lambda k: sum(mean_ms[i] for i in groups[k]))
+    members = groups[dom_kernel]
+    achieved = (sum(entries[i]["bytes"] for i in members)
+                / (sum(mean_ms[i] for i in members) * 1e-3) / 1e9)
+    share = sum(mean_ms[i] for i in members) / float(np.sum(mean_ms))
+    # DRAM traffic per launch from an ncu capture of one of its plans (the
+    # slowest one that has a record for the current kernel sources)
+    by_time = sorted(members, key=lambda i: -mean_ms[i])
+    d = next((entries[i] for i in by_time
+              if ncu_traffic(entries[i]["label"], dom_kernel) is not None),
+             entries[by_time[0]])
     detail = {}
     for i, e in enumerate(entries):
         gbs = e["bytes"] / (mean_ms[i] * 1e-3) / 1e9
@@ -478,7 +542,9 @@ def run_ours(args, rank, world, local_rank):
         "gflops": round(world * step_flops / (ms_per_step * 1e-3) / 1e9, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "kernel": d["label"], "traffic": ncu_traffic(d["label"])},
+                     "kernel": dom_kernel, "share_of_step": round(share, 3),
+                     "plans": [entries[i]["label"] for i in members],
+                     "traffic": ncu_traffic(d["label"], dom_kernel), "traffic_plan": d["label"]},
         "gpu_launches": int(args.steps * sum(e["info"]["launches_per_exec"] for e in entries)),
         "clocks": clk,
         "e2e": e2e,
@@ -489,9 +555,42 @@ def run_ours(args, rank, world, local_rank):
     }
     if args.workload == "precision":
         line["cg_ir"] = precision_solves(S, mats[0], parts_kept, dev, log)
+    if args.workload == "batching":
+        line["graph"] = graph_replay(S, [e for e in entries if "batch_split" in e["label"]][0],
+                                     stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(mats, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+def graph_replay(S, e, stream, iters=100, reps=5):
+    """100 repeated products of one plan captured in a CUDA graph; the time
+    per product of a replay (median of reps replays)."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        S.spmv_exec(e["plan"], e["xh"], e["yh"])
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(iters):
+            S.spmv_exec(e["plan"], e["xh"], e["yh"])
+    ts = []
+    with torch.cuda.stream(s):          # replay() launches on the current stream
+        g.replay()
+        torch.cuda.synchronize()
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            g.replay()
+            b.record(s)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+    us = 1e3 * float(np.median(ts)) / iters
+    return {"plan": e["label"], "iterations": iters, "us_per_product": round(us, 2),
+            "GBps": round(e["bytes"] / (us * 1e-6) / 1e9, 1),
+            "launches_per_product": e["info"]["launches_per_exec"]}
 
 
 def precision_solves(S, mat, parts, dev, log):
@@ -547,8 +646,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="tiled forms with the default tile shape instead of the autotuned one")
-    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 256, 1024],
-                    help="tiled forms with this CTA shape instead of the autotuned one")
+    ap.add_argument("--shape", default="", choices=["", "cta256", "cta1024", "cta256x8"],
+                    help="tiled forms with this tile shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")
     args = ap.parse_args()

@@ -166,6 +166,7 @@ typedef struct spmv_plan_info {
     int64_t compulsory_bytes;   /* nnz*(value+4) + (m+1)*4 + n*r*xb + m*r*yb */
     int64_t moved_bytes;        /* bytes one exec reads/writes if every array
                                    element it touches is moved once */
+    int32_t cta_threads;        /* tiled kernel CTA size (0: plain CSR kernel) */
 } spmv_plan_info;
 
 /* Build a plan: validate A, the permutation and the form (eqs. 1, 2, 5 or
@@ -178,6 +179,21 @@ typedef struct spmv_plan_info {
 spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm,
                              const spmv_splits *splits, const spmv_opts *opts,
                              spmv_plan **out);
+
+/* Batched plan (not in the paper): `count` independent matrices A[b], each
+ * with its own perms[b] (NULL array or NULL members = identity) and, for the
+ * split form, splits[b] (all with the same K; splits NULL = natural form),
+ * in one plan whose spmv_exec is one launch over all of them.  The plan is
+ * the block-diagonal matrix diag(A[0], ..., A[count-1]); x_hat is the
+ * concatenation of the matrices' x_hat (n[b]*r entries each, in order) and
+ * y_hat that of their y_hat.  For the split form, part k of the batch is the
+ * union of the matrices' parts k: it is itself a nonzero-disjoint split
+ * (Sec. 4) of the block-diagonal matrix.  SB / DB are not batched (each
+ * matrix's border would have to share one border): SPMV_E_UNSUPPORTED.
+ * Other errors as spmv_plan_create, with the matrix index in the message. */
+spmv_status spmv_plan_create_batched(int32_t count, const spmv_csr *A, const spmv_perm *perms,
+                                     const spmv_splits *splits, const spmv_opts *opts,
+                                     spmv_plan **out);
 
 /* y_hat <- A_hat x_hat (Sec. 3), or y_hat <- 0; y_hat <- y_hat + A^k x_hat for
  * k = 1..K (Sec. 4), on `stream`.  x_hat: n*r device elements, y_hat: m*r

@@ -15,6 +15,7 @@ Function names follow the C ABI:
     spmv_exec_host        the same with host buffers (copies inside)
     spmv_plan_check       report a device wait that gave up (SPMV_E_TIMEOUT)
     spmv_cg_ir            mixed-precision CG with FP64 iterative refinement
+    spmv_plan_create_batched  many matrices in one plan (one launch per exec)
     spmv_permute_x / spmv_unpermute_y
     spmv_plan_get_info / spmv_plan_destroy / spmv_last_error
 """
@@ -47,7 +48,7 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
            "spmv_form_from_labels", "spmv_partition", "spmv_partition_free",
            "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
-           "spmv_plan_check", "spmv_cg_ir")
+           "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
@@ -96,7 +97,8 @@ class spmv_plan_info(ctypes.Structure):
                 ("smem_bytes", ctypes.c_int32), ("staged_entries", ctypes.c_int64),
                 ("list_entries", ctypes.c_int64), ("partial_slots", ctypes.c_int64),
                 ("fixup_rows", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("compulsory_bytes", ctypes.c_int64), ("moved_bytes", ctypes.c_int64)]
+                ("compulsory_bytes", ctypes.c_int64), ("moved_bytes", ctypes.c_int64),
+                ("cta_threads", ctypes.c_int32)]
 
 
 class spmv_partition_opts(ctypes.Structure):
@@ -137,6 +139,9 @@ def _load():
     L.spmv_exec.argtypes = [vp, vp, vp, vp]
     L.spmv_exec_host.argtypes = [vp, vp, vp, vp]
     L.spmv_plan_check.argtypes = [vp, vp]
+    L.spmv_plan_create_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(spmv_csr),
+                                           ctypes.POINTER(spmv_perm), ctypes.POINTER(spmv_splits),
+                                           ctypes.POINTER(spmv_opts), ctypes.POINTER(vp)]
     L.spmv_cg_ir.argtypes = [vp, vp, vp, vp, ctypes.POINTER(spmv_cg_opts),
                              ctypes.POINTER(spmv_cg_info), vp]
     L.spmv_permute_x.argtypes = [vp, vp, vp, vp]
@@ -160,7 +165,8 @@ def _load():
     for name in ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
                  "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
                  "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
-                 "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir"):
+                 "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir",
+                 "spmv_plan_create_batched"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -266,6 +272,47 @@ def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
     handle = ctypes.c_void_p()
     _check(lib.spmv_plan_create(ctypes.byref(A), ctypes.byref(perm), ctypes.byref(splits),
                                 ctypes.byref(opts), ctypes.byref(handle)))
+    plan = Plan(handle, None)
+    plan.info = spmv_plan_get_info(plan)
+    return plan
+
+
+def spmv_plan_create_batched(mats, perms=None, nz_parts=None, K=0, dtype=SPMV_F64, nrhs=1,
+                             tile_cols=0, tile_nnz=0, long_row=0, lanes=0, flags=0,
+                             cta_threads=0, allocator="torch"):
+    """One plan over the block-diagonal matrix of `mats` (a list of
+    (m, n, rowptr, colidx, vals)); perms: None or a list of (row_perm,
+    col_perm) pairs (None members = identity); nz_parts: None (natural form)
+    or a list of per-matrix nonzero labels in [0, K) (split form).  x_hat and
+    y_hat of the plan are the matrices' vectors back to back."""
+    cnt = len(mats)
+    csrs = (spmv_csr * cnt)()
+    keep = []
+    for b, (m, n, rp, ci, v) in enumerate(mats):
+        A, k = _csr_struct(m, n, rp, ci, v)
+        csrs[b] = A
+        keep.append(k)
+    pp = None
+    if perms is not None:
+        pp = (spmv_perm * cnt)()
+        for b, pr in enumerate(perms):
+            rperm = None if pr is None or pr[0] is None else _i32(pr[0])
+            cperm = None if pr is None or pr[1] is None else _i32(pr[1])
+            keep.append((rperm, cperm))
+            pp[b] = spmv_perm(_ptr(rperm), _ptr(cperm))
+    sp = None
+    if nz_parts is not None:
+        sp = (spmv_splits * cnt)()
+        for b, lab in enumerate(nz_parts):
+            nzp = _i32(lab)
+            keep.append(nzp)
+            sp[b] = spmv_splits(SPMV_SPLIT, K, None, None, _ptr(nzp))
+    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, cta_threads)
+    if allocator == "torch":
+        opts.alloc, opts.release = _ALLOC_CB, _FREE_CB
+    handle = ctypes.c_void_p()
+    _check(lib.spmv_plan_create_batched(cnt, csrs, pp, sp, ctypes.byref(opts),
+                                        ctypes.byref(handle)))
     plan = Plan(handle, None)
     plan.info = spmv_plan_get_info(plan)
     return plan

@@ -309,6 +309,7 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         I.n_chunk_tiles = hp.n_chunk_tiles;
         I.launches_per_exec = hp.m == 0 ? 0 : (tiled ? (dp.n_tiles > 0) + (dp.n_fixups > 0) : 1);
         I.smem_bytes = dp.smem_bytes;
+        I.cta_threads = tiled ? hp.cta_threads : 0;
         I.staged_entries = hp.staged_entries;
         I.list_entries = hp.list_entries;
         I.partial_slots = hp.partial_slots;

@@ -52,6 +52,10 @@ constexpr int kWideThreads = 1024;
 #ifndef SPMV_TILE_MINBLOCKS
 #define SPMV_TILE_MINBLOCKS 6
 #endif
+//   SPMV_L1_PREF      1 = ask for the largest L1 carveout for the tile kernels
+#ifndef SPMV_L1_PREF
+#define SPMV_L1_PREF 0
+#endif
 // resident 256-thread tile CTAs per SM the register budget is sized for:
 // fewer for many right-hand sides, which hold r accumulators per lane
 constexpr int tile_ctas_per_sm(int r)
@@ -681,6 +685,24 @@ k_fixup(const Fixup *__restrict__ f, const int32_t nf, const XT *__restrict__ pa
 template <class Kern>
 inline cudaError_t ensure_smem(Kern k, int bytes)
 {
+#if SPMV_L1_PREF
+    {
+        // prefer the largest L1 (a hint; launches that need more shared
+        // memory still get it)
+        static std::mutex mu1;
+        static std::map<std::pair<const void *, int>, bool> pref;
+        int dev1 = 0;
+        cudaError_t e1 = cudaGetDevice(&dev1);
+        if (e1 != cudaSuccess) return e1;
+        std::lock_guard<std::mutex> g1(mu1);
+        const auto key1 = std::make_pair(reinterpret_cast<const void *>(k), dev1);
+        if (!pref.count(key1)) {
+            e1 = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+            if (e1 != cudaSuccess) return e1;
+            pref[key1] = true;
+        }
+    }
+#endif
     if (bytes <= 0) return cudaSuccess;
     // one cache per kernel instance (the template is shared by every kernel
     // with the same signature, so the key is the kernel's address)

@@ -261,3 +261,36 @@ def laplacian3d(n=128, seed=0, permute=True):
         inv[perm] = np.arange(N)
         rows, cols = inv[rows], inv[cols]
     return coo_to_csr(N, N, rows, cols, vals)
+
+
+def rmat_batch(count=64, lo=1024, hi=65536, deg_lo=8, deg_hi=32, seed=0):
+    """`count` R-MAT matrices (a, b, c = .57, .19, .19) with row counts drawn
+    log-uniformly in [lo, hi] and rounded to a power of two (R-MAT's own
+    sizes), average degree uniform in [deg_lo, deg_hi], seeds seed..seed+count-1.
+    Returns a list of (m, n, rowptr, colidx, vals)."""
+    rng = _rng(seed)
+    out = []
+    for b in range(count):
+        scale = int(round(rng.uniform(np.log2(lo), np.log2(hi))))
+        deg = int(rng.integers(deg_lo, deg_hi + 1))
+        rp, ci, v = rmat(scale, deg, seed=seed + b, chunk=1 << 18)
+        out.append((1 << scale, 1 << scale, rp, ci, v))
+    return out
+
+
+def block_diagonal(mats):
+    """CSR of diag(A_1, ..., A_B) from a list of (m, n, rowptr, colidx, vals)."""
+    M = sum(m for m, *_ in mats)
+    rps, cis, vs = [np.zeros(1, dtype=np.int64)], [], []
+    r_off = c_off = e_off = 0
+    for m, n, rp, ci, v in mats:
+        rps.append(rp[1:].astype(np.int64) + e_off)
+        cis.append(ci.astype(np.int64) + c_off)
+        vs.append(v)
+        c_off += n
+        e_off += int(rp[-1])
+        r_off += m
+    rowptr = np.concatenate(rps)
+    assert rowptr.size == M + 1
+    return rowptr.astype(np.int32), np.concatenate(cis).astype(np.int32), np.concatenate(vs)
+

@@ -101,3 +101,21 @@ def test_plan_create_validation_before_any_device_call():
     assert st == S.SPMV_E_STRUCTURE
     st, _ = _plan_status(form=S.SPMV_SPLIT, K=2, nz_part=np.array([0, 1, 2, 0, 0, 0, 0]))
     assert st == S.SPMV_E_INVALID
+
+
+def test_batched_plan_validation_before_any_device_call():
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 1], dtype=np.int32)
+    v = np.ones(2)
+    mats = [(2, 2, rp, ci, v), (2, 2, rp, ci, v)]
+    with pytest.raises(S.SpmvError) as e:
+        S.spmv_plan_create_batched(mats, nz_parts=[np.array([0, 2]), np.array([0, 1])], K=2)
+    assert e.value.status == S.SPMV_E_INVALID and "matrix 0" in str(e.value)
+    bad = [(2, 2, rp, ci, v), (2, 2, np.array([0, 2, 1], dtype=np.int32), ci, v)]
+    with pytest.raises(S.SpmvError) as e:
+        S.spmv_plan_create_batched(bad)
+    assert e.value.status == S.SPMV_E_INVALID and "matrix 1" in str(e.value)
+    with pytest.raises(S.SpmvError) as e:
+        S.spmv_plan_create_batched(mats, perms=[(np.array([0, 2]), None), None])
+    assert e.value.status == S.SPMV_E_STRUCTURE
+
