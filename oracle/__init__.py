@@ -84,6 +84,8 @@ def lib():
         L.ref_cg.argtypes = [_i32, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_double,
                              _i32, ctypes.POINTER(ctypes.c_double)]
         L.ref_cg.restype = _i32
+        L.ref_mlp_loss_grad.argtypes = [_i32, _i32, _i32, _i32, _f64p, _i32p] + [_f64p] * 13
+        L.ref_mlp_loss_grad.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -294,3 +296,19 @@ def cg(n, rowptr, colidx, vals, b, x0=None, tol=1e-10, maxit=10000):
     it = lib().ref_cg(n, rp, ci, v, np.ascontiguousarray(b, dtype=np.float64), x, tol, maxit,
                       ctypes.byref(rel))
     return x, int(it), rel.value
+
+
+def mlp_loss_grad(X, labels, params, grads=True):
+    """Selector network (extension): params = (W1, b1, W2, b2, W3, b3) with
+    W row major [out][in]; returns (loss, logits, grads or None), FP64."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    W1, b1, W2, b2, W3, b3 = [np.ascontiguousarray(p, dtype=np.float64) for p in params]
+    batch, nin = X.shape
+    nh, nc = W1.shape[0], W3.shape[0]
+    logits = np.zeros((batch, nc))
+    g = [np.zeros_like(p) for p in (W1, b1, W2, b2, W3, b3)]
+    loss = lib().ref_mlp_loss_grad(batch, nin, nh, nc, X, labels, W1, b1, W2, b2, W3, b3,
+                                   *g, logits)
+    return loss, logits, (g if grads else None)
+

@@ -22,6 +22,9 @@
  *                       access order (Sec. 2.2, Sec. 3 fully-associative
  *                       assumption), counting misses per array.
  *   ref_cg              conjugate gradients in FP64 (iterative solvers, Sec. 1).
+ *   ref_mlp_loss_grad   the selector extension's multilayer perceptron (not in
+ *                       the paper): forward pass, softmax cross-entropy, and
+ *                       the gradients by the chain rule, in FP64.
  */
 #include <math.h>
 #include <stdint.h>
@@ -580,3 +583,103 @@ int32_t ref_cg(int32_t n, const int64_t *rowptr, const int32_t *col,
     free(r); free(p); free(q);
     return it;
 }
+
+
+/* ------------------------------------------------------------------ MLP --- */
+
+/* Selector network (an extension; the paper has no learned component):
+ *   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), z = W3 h2 + b3,
+ *   loss = mean over the batch of -log softmax(z)[label].
+ * W1 is nh x nin, W2 nh x nh, W3 nc x nh, row major ([out][in]).  Returns the
+ * loss; writes the logits (batch x nc) if `logits` is not NULL and the
+ * gradients of the loss if gW1 is not NULL.  Plain loops, FP64. */
+double ref_mlp_loss_grad(int32_t batch, int32_t nin, int32_t nh, int32_t nc,
+                         const double *X, const int32_t *labels,
+                         const double *W1, const double *b1, const double *W2,
+                         const double *b2, const double *W3, const double *b3,
+                         double *gW1, double *gb1, double *gW2, double *gb2,
+                         double *gW3, double *gb3, double *logits)
+{
+    double *h1 = (double *)calloc((size_t)batch * nh, sizeof(double));
+    double *h2 = (double *)calloc((size_t)batch * nh, sizeof(double));
+    double *z = (double *)calloc((size_t)batch * nc, sizeof(double));
+    double *dz = (double *)calloc((size_t)batch * nc, sizeof(double));
+    double *d2 = (double *)calloc((size_t)batch * nh, sizeof(double));
+    double *d1 = (double *)calloc((size_t)batch * nh, sizeof(double));
+    double loss = 0.0;
+    for (int32_t b = 0; b < batch; ++b) {
+        const double *x = X + (size_t)b * nin;
+        for (int32_t o = 0; o < nh; ++o) {
+            double a = b1[o];
+            for (int32_t i = 0; i < nin; ++i) a += W1[(size_t)o * nin + i] * x[i];
+            h1[(size_t)b * nh + o] = a > 0.0 ? a : 0.0;
+        }
+        for (int32_t o = 0; o < nh; ++o) {
+            double a = b2[o];
+            for (int32_t i = 0; i < nh; ++i) a += W2[(size_t)o * nh + i] * h1[(size_t)b * nh + i];
+            h2[(size_t)b * nh + o] = a > 0.0 ? a : 0.0;
+        }
+        double zmax = -INFINITY;
+        for (int32_t o = 0; o < nc; ++o) {
+            double a = b3[o];
+            for (int32_t i = 0; i < nh; ++i) a += W3[(size_t)o * nh + i] * h2[(size_t)b * nh + i];
+            z[(size_t)b * nc + o] = a;
+            if (a > zmax) zmax = a;
+        }
+        double se = 0.0;
+        for (int32_t o = 0; o < nc; ++o) se += exp(z[(size_t)b * nc + o] - zmax);
+        const double lse = zmax + log(se);
+        loss += lse - z[(size_t)b * nc + labels[b]];
+        /* d loss / d z = (softmax - onehot) / batch */
+        for (int32_t o = 0; o < nc; ++o) {
+            const double p = exp(z[(size_t)b * nc + o] - lse);
+            dz[(size_t)b * nc + o] = (p - (o == labels[b] ? 1.0 : 0.0)) / batch;
+        }
+    }
+    loss /= batch;
+    if (logits) memcpy(logits, z, (size_t)batch * nc * sizeof(double));
+    if (gW1) {
+        memset(gW3, 0, (size_t)nc * nh * sizeof(double));
+        memset(gb3, 0, (size_t)nc * sizeof(double));
+        memset(gW2, 0, (size_t)nh * nh * sizeof(double));
+        memset(gb2, 0, (size_t)nh * sizeof(double));
+        memset(gW1, 0, (size_t)nh * nin * sizeof(double));
+        memset(gb1, 0, (size_t)nh * sizeof(double));
+        for (int32_t b = 0; b < batch; ++b) {
+            for (int32_t o = 0; o < nc; ++o) {
+                const double g = dz[(size_t)b * nc + o];
+                gb3[o] += g;
+                for (int32_t i = 0; i < nh; ++i) gW3[(size_t)o * nh + i] += g * h2[(size_t)b * nh + i];
+            }
+            for (int32_t i = 0; i < nh; ++i) {
+                double a = 0.0;
+                for (int32_t o = 0; o < nc; ++o) a += dz[(size_t)b * nc + o] * W3[(size_t)o * nh + i];
+                d2[(size_t)b * nh + i] = h2[(size_t)b * nh + i] > 0.0 ? a : 0.0;
+            }
+            for (int32_t o = 0; o < nh; ++o) {
+                const double g = d2[(size_t)b * nh + o];
+                gb2[o] += g;
+                for (int32_t i = 0; i < nh; ++i) gW2[(size_t)o * nh + i] += g * h1[(size_t)b * nh + i];
+            }
+            for (int32_t i = 0; i < nh; ++i) {
+                double a = 0.0;
+                for (int32_t o = 0; o < nh; ++o) a += d2[(size_t)b * nh + o] * W2[(size_t)o * nh + i];
+                d1[(size_t)b * nh + i] = h1[(size_t)b * nh + i] > 0.0 ? a : 0.0;
+            }
+            for (int32_t o = 0; o < nh; ++o) {
+                const double g = d1[(size_t)b * nh + o];
+                gb1[o] += g;
+                for (int32_t i = 0; i < nin; ++i)
+                    gW1[(size_t)o * nin + i] += g * X[(size_t)b * nin + i];
+            }
+        }
+    }
+    free(h1);
+    free(h2);
+    free(z);
+    free(dz);
+    free(d2);
+    free(d1);
+    return loss;
+}
+

@@ -394,3 +394,53 @@ def test_zipf_row_degrees():
     deg = np.diff(rp)
     assert deg.max() <= 512 and deg.min() >= 1
     assert 6.5 < deg.mean() < 9.5
+
+
+# ------------------------------------------------ selector MLP (extension) ---
+def _mlp_params(rng, nin, nh, nc, scale=0.5):
+    return [rng.normal(0, scale, (nh, nin)), rng.normal(0, scale, nh),
+            rng.normal(0, scale, (nh, nh)), rng.normal(0, scale, nh),
+            rng.normal(0, scale, (nc, nh)), rng.normal(0, scale, nc)]
+
+
+def test_mlp_gradients_match_finite_differences():
+    # central differences of the loss pin every gradient, independently of
+    # the chain-rule code under test
+    rng = np.random.default_rng(5)
+    nin, nh, nc, batch = 3, 4, 3, 5
+    X = rng.normal(0, 1, (batch, nin))
+    y = rng.integers(0, nc, batch)
+    params = _mlp_params(rng, nin, nh, nc)
+    _, _, grads = oracle.mlp_loss_grad(X, y, params)
+    h = 1e-6
+    for p, g in zip(params, grads):
+        flat, gflat = p.reshape(-1), g.reshape(-1)
+        for k in range(flat.size):
+            old = flat[k]
+            flat[k] = old + h
+            lp = oracle.mlp_loss_grad(X, y, params, grads=False)[0]
+            flat[k] = old - h
+            lm = oracle.mlp_loss_grad(X, y, params, grads=False)[0]
+            flat[k] = old
+            assert abs((lp - lm) / (2 * h) - gflat[k]) <= 1e-7 * max(1.0, abs(gflat[k]))
+
+
+def test_mlp_loss_closed_forms():
+    rng = np.random.default_rng(6)
+    nin, nh, nc, batch = 4, 5, 7, 6
+    X = rng.normal(0, 1, (batch, nin))
+    y = rng.integers(0, nc, batch)
+    zero = [np.zeros_like(p) for p in _mlp_params(rng, nin, nh, nc)]
+    loss, logits, grads = oracle.mlp_loss_grad(X, y, zero)
+    # all logits zero: softmax uniform, loss log(nc); only b3 gets a gradient
+    assert abs(loss - np.log(nc)) < 1e-14 and not np.any(logits)
+    onehot = np.zeros((batch, nc))
+    onehot[np.arange(batch), y] = 1.0
+    assert np.allclose(grads[5], (1.0 / nc - onehot).mean(axis=0), atol=1e-15)
+    assert not np.any(grads[0]) and not np.any(grads[4])
+    # a network that only passes b3: logits = b3 for every sample
+    b3 = rng.normal(0, 1, nc)
+    loss, logits, _ = oracle.mlp_loss_grad(X, y, zero[:5] + [b3])
+    lse = np.log(np.exp(b3).sum())
+    assert abs(loss - np.mean(lse - b3[y])) < 1e-13
+    assert np.allclose(logits, np.tile(b3, (batch, 1)))
