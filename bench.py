@@ -391,10 +391,12 @@ def run_ours(args, rank, world, local_rank):
             kw, pres = form_kwargs(S, f, rp, ci, parts)
             t1 = time.perf_counter()
             chosen = None
-            # tile shapes: one wave of 256-thread tiles, wide tiles, or eight
-            # waves of smaller tiles (launched in order, so that the x windows
-            # of the tiles running at once stay within L2 when x does not)
-            shapes = {"cta256": dict(dtype=dtype), "cta1024": dict(dtype=dtype, cta_threads=1024),
+            # tile shapes: one wave of 256-thread tiles (staging nothing, or
+            # staging x), wide tiles, or eight waves of smaller tiles (launched in order, so that the x windows of the
+            # tiles running at once stay within L2 when x does not)
+            shapes = {"cta256": dict(dtype=dtype),
+                      "cta256s": dict(dtype=dtype, flags=S.SPMV_FLAG_STAGE),
+                      "cta1024": dict(dtype=dtype, cta_threads=1024),
                       "cta256x8": dict(dtype=dtype,
                                        tile_nnz=max(1024, int(rp[-1]) // (8 * 912)))}
             if f.startswith("batch_split"):
@@ -421,7 +423,8 @@ def run_ours(args, rank, world, local_rank):
             entries.append(dict(label="%s/%s" % (name, f), plan=plan, xh=xh, yh=yh,
                                 bytes=compulsory_bytes(m, n, int(rp[-1]), vb, xb),
                                 flops=2 * int(rp[-1]), err=err, info=info, tile_shape=chosen,
-                                cost=None if pres is None else int(pres["cost"])))
+                                cost=None if pres is None else int(pres["cost"]),
+                                part_s=None if pres is None else float(pres["seconds"])))
             log("  plan %s/%s: K=%d tiles=%d staged=%d shape=%s err=%.2e (%.1fs)" % (
                 name, f, info["K"], info["n_tiles"], info["n_staged_tiles"], chosen, err,
                 time.perf_counter() - t1))
@@ -528,6 +531,17 @@ def run_ours(args, rank, world, local_rank):
     speedup = {mat: {"best_form": best[mat][0],
                      "speedup_vs_natural": round(detail[mat + "/natural"]["us"] / best[mat][1], 3)
                      if (mat + "/natural") in detail else None} for mat in best}
+    # the paper's Table 3 analogue: partitioning time on the host, and the
+    # number of products after which a form has paid for it against plain
+    # CSR in natural order
+    for e in entries:
+        dd = detail[e["label"]]
+        nat = detail.get(e["label"].split("/")[0] + "/natural")
+        dd["partition_s"] = None if e["part_s"] is None else round(e["part_s"], 2)
+        gain_us = None if nat is None else nat["us"] - dd["us"]
+        dd["amortized_after_spmvs"] = (int(np.ceil(e["part_s"] * 1e6 / gain_us))
+                                       if e["part_s"] is not None and gain_us and gain_us > 0
+                                       else None)
     line = {
         "metric": "SpMV GB/s (compulsory bytes; % of GB300 HBM roofline)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -631,13 +645,154 @@ def precision_solves(S, mat, parts, dev, log):
     return out
 
 
+# ------------------------------------------------------------- selector --
+def selector_matrix(i):
+    """Seeded matrix i of the selector's data: mesh, R-MAT, blocks or Zipf
+    families with 10^4 .. 10^5 rows, taking turns."""
+    g = np.random.default_rng(1000 + i)
+    fam = i % 4
+    if fam == 0:
+        nx = int(g.integers(100, 317))
+        rp, ci, v = synth.mesh5(nx, seed=i)
+    elif fam == 1:
+        rp, ci, v = synth.rmat(int(g.integers(13, 17)), int(g.integers(4, 17)), seed=i,
+                               chunk=1 << 18)
+    elif fam == 2:
+        nb = int(g.choice([8, 16, 32, 64]))
+        bs = int(g.integers(10000, 50001)) // nb
+        rp, ci, v = synth.blocks(nb, bs, float(g.uniform(8, 24)) / bs, 0.05, seed=i)
+    else:
+        m = int(g.integers(10000, 100001))
+        rp, ci, v = synth.zipf_matrix(m, m, seed=i)
+    return rp, ci, v
+
+
+def _selector_partitions(i):
+    """Worker (spawned process, no GPU): the matrix and the partitions its
+    classes need."""
+    import paper_1203_2739_gb300 as S
+    rp, ci, v = selector_matrix(i)
+    m = n = len(rp) - 1
+    out = {}
+    for meth, K in ((S.SPMV_PART_CN, 16), (S.SPMV_PART_CN, 256), (S.SPMV_PART_ERCN, 16),
+                    (S.SPMV_PART_ERCN, 256), (S.SPMV_PART_RCN, 256)):
+        out[(meth, K)] = S.spmv_partition(m, n, rp, ci, meth, K=K, seed=0, threads=1)
+    return i, out
+
+
+def run_selector(args, pool_results):
+    """Train the selector on autotuner timings of the first 3/4 of the
+    matrices and evaluate it on the rest: regret against the exhaustive
+    optimum, and throughput against plain CSR."""
+    import torch
+    import paper_1203_2739_gb300 as S
+    import paper_1203_2739_gb300.selector as SEL
+    log = lambda s: print(s, file=sys.stderr, flush=True)   # noqa: E731
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    N = len(pool_results)
+    feats, times, nbytes = [], [], []
+    t_setup = time.perf_counter()
+    for i in range(N):
+        rp, ci, v = selector_matrix(i)
+        m = n = len(rp) - 1
+        parts = pool_results[i]
+        feats.append(S.spmv_features(m, n, rp, ci))
+        x = torch.from_numpy(synth.uniform_x(n, 1)).to(dev)
+        y = torch.empty(m, dtype=torch.float64, device=dev)
+        row = []
+        for fw, K, ct in SEL.CLASSES:
+            if fw == "natural":
+                kw = {}
+            elif fw in ("sb", "db"):
+                r = parts[(S.SPMV_PART_CN if fw == "sb" else S.SPMV_PART_ERCN, K)]
+                kw = dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"],
+                          K=r["K"], row_part_ptr=r["row_part_ptr"],
+                          col_part_ptr=r["col_part_ptr"], cta_threads=ct)
+            else:
+                full = parts[(S.SPMV_PART_RCN, 256)]
+                lab = (full["labels"] // (256 // K)).astype(np.int32)
+                rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SPLIT, K,
+                                                                 lab)
+                kw = dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SPLIT, K=K,
+                          row_part_ptr=rpp, col_part_ptr=cpp, nz_part=lab, cta_threads=ct)
+            plan = S.spmv_plan_create(m, n, rp, ci, v, **kw)
+            for _ in range(3):
+                S.spmv_exec(plan, x, y)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            a.record(stream)
+            for _ in range(reps):
+                S.spmv_exec(plan, x, y)
+            b.record(stream)
+            torch.cuda.synchronize()
+            row.append(a.elapsed_time(b) / reps)
+            del plan
+        times.append(row)
+        nbytes.append(compulsory_bytes(m, n, int(rp[-1])))
+        if i % 16 == 15:
+            log("  selector data: %d/%d matrices timed" % (i + 1, N))
+    setup_s = time.perf_counter() - t_setup
+    F, T = np.array(feats), np.array(times)
+    best = T.argmin(axis=1)
+    ntr = (3 * N) // 4
+    sel = SEL.Selector(seed=0)
+    t0 = time.perf_counter()
+    hist = sel.fit(F[:ntr], best[:ntr], epochs=400, lr=3e-3, batch=32)
+    train_s = time.perf_counter() - t0
+    test = np.arange(ntr, N)
+    p = sel.proba(F[test])
+    pick = p.argmax(axis=1)
+    conf = p.max(axis=1)
+    regret = T[test, pick] / T[test, best[test]] - 1.0
+    # fallback: below the confidence threshold, time every class (regret 0)
+    thr = 0.5
+    regret_fb = np.where(conf >= thr, regret, 0.0)
+    t_pick = T[test, pick].sum()
+    t_plain = T[test, 0].sum()
+    t_best = T[test, best[test]].sum()
+    bytes_test = float(np.sum(np.array(nbytes)[test]))
+    line = {
+        "metric": "SpMV GB/s (compulsory bytes) of the selector's choice on held-out matrices",
+        "value": round(bytes_test / (t_pick * 1e-3) / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
+        "steps": 20, "warmup": 3, "ms_per_step": round(float(t_pick), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "learned selector: %d seeded matrices (mesh / R-MAT / blocks / "
+                               "Zipf, 1e4-1e5 rows), %d classes (plain CSR; SB, DB, split at "
+                               "K = 16, 256; 256- or 1024-thread tiles); trained on %d, "
+                               "evaluated on %d" % (N, len(SEL.CLASSES), ntr, N - ntr),
+                   "l2": "matrices smaller than L2: repeated products with L2 warm"},
+        "selector": {
+            "regret_mean": round(float(regret.mean()), 4),
+            "regret_median": round(float(np.median(regret)), 4),
+            "within_10pct": round(float((regret <= 0.10).mean()), 3),
+            "regret_mean_with_fallback": round(float(regret_fb.mean()), 4),
+            "fallback_share": round(float((conf < thr).mean()), 3),
+            "top1_accuracy": round(float((pick == best[test]).mean()), 3),
+            "speedup_vs_plain_csr": round(float(t_plain / t_pick), 3),
+            "speedup_vs_plain_csr_oracle_choice": round(float(t_plain / t_best), 3),
+            "speedup_vs_best_fixed_class": round(float(
+                T[test].sum(axis=0).min() / t_pick), 3),
+            "train_loss_first_last": [round(hist[0], 4), round(hist[-1], 4)],
+            "train_seconds_gpu_kernels": round(train_s, 2),
+            "data_seconds": round(setup_s, 1)},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=sorted(MATRICES))
+    ap.add_argument("--workload", default="sweep", choices=sorted(MATRICES) + ["selector"])
+    ap.add_argument("--selector-matrices", type=int, default=96)
+    ap.add_argument("--scale-nx", type=int, default=6144,
+                    help="grid side of the scale workload's mesh (x exceeds L2 from about 4096)")
     ap.add_argument("--forms", default="")
     ap.add_argument("--matrices", default="", help="subset of the workload's matrices (by name)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
@@ -646,14 +801,28 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="tiled forms with the default tile shape instead of the autotuned one")
-    ap.add_argument("--shape", default="", choices=["", "cta256", "cta1024", "cta256x8"],
+    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256s", "cta1024",
+                                                    "cta256x8"],
                     help="tiled forms with this tile shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")
     args = ap.parse_args()
+    if args.scale_nx != 6144:
+        nx = args.scale_nx
+        MATRICES["scale"] = [("mesh5_%d" % nx, lambda: synth.mesh5(nx, seed=0))]
+        WORKLOAD_TEXT["scale"] = WORKLOAD_TEXT["scale"].replace(
+            "mesh 6144^2 (37.7M rows, 188.7M nnz, x = 302 MB)", "mesh %d^2" % nx)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "selector":
+        # partitions on host processes started before any GPU work
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(max(1, (os.cpu_count() or 4))) as pool:
+            res = dict(pool.map(_selector_partitions, range(args.selector_matrices)))
+        run_selector(args, [res[i] for i in range(args.selector_matrices)])
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

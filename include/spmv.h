@@ -79,9 +79,12 @@ enum {
                                     default is one CTA per tile, with tiles
                                     sized so that they fill about one wave of
                                     resident CTAs */
-    SPMV_FLAG_STAGE = 16         /* stage x in 256-thread CTAs too; by default
-                                    only wide (1024-thread) CTAs stage, where
-                                    the window is large enough to pay */
+    SPMV_FLAG_STAGE = 16         /* stage x in 256-thread CTAs too (every
+                                    column of a tile when they fit, with
+                                    16-bit indices; else the entries that pay);
+                                    by default only wide 1024-thread CTAs
+                                    stage, where the window is large enough
+                                    to pay on GB300 */
 };
 
 /* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,
@@ -264,6 +267,51 @@ typedef struct spmv_cg_info {
 
 spmv_status spmv_cg_ir(spmv_plan *low, spmv_plan *f64, const double *b, double *x,
                        const spmv_cg_opts *opts, spmv_cg_info *info, void *stream);
+
+/* ---- Learned form selector (not in the paper, which chooses its methods
+ * by experiment, Sec. 5).  A multilayer perceptron maps SPMV_SEL_FEATURES
+ * features of a matrix to scores of (form, K, tile shape) classes; it is
+ * trained on the GPU by the kernels below from autotuner timings. */
+enum { SPMV_SEL_FEATURES = 16 };
+
+/* Features of a host CSR matrix (validated as for spmv_plan_create), into
+ * out[SPMV_SEL_FEATURES]: log2 of m, n, nnz; row-degree mean, coefficient of
+ * variation, log2 max, max/mean; column-degree coefficient of variation,
+ * log2 max, max/mean; mean |j - i n/m| / n; share of nonzeros within n/64 of
+ * the diagonal; share of touched columns used by more than one of 16
+ * contiguous row blocks; share of empty rows; share of nonzeros in rows
+ * longer than 64; log2 of the CSR bytes relative to 128 MB.  Host only. */
+spmv_status spmv_features(const spmv_csr *A, float *out);
+
+/* The network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), z = W3 h2 + b3,
+ * FP32, W row major [out][in]; `params` is ONE device array holding W1
+ * (nh x nin), b1, W2 (nh x nh), b2, W3 (nc x nh), b3 back to back
+ * (spmv_mlp_param_count(nin, nh, nc) floats).  Caller-owned. */
+typedef struct spmv_mlp {
+    int32_t nin, nh, nc;
+    float *params;
+} spmv_mlp;
+
+int64_t spmv_mlp_param_count(int32_t nin, int32_t nh, int32_t nc);
+/* Device workspace bytes spmv_mlp_forward / spmv_mlp_grad need for `batch`. */
+size_t spmv_mlp_work_bytes(int32_t nh, int32_t nc, int32_t batch);
+
+/* logits (batch x nc) = net(X), X batch x nin; device pointers; async. */
+spmv_status spmv_mlp_forward(const spmv_mlp *net, const float *X, int32_t batch,
+                             float *logits, void *work, void *stream);
+
+/* Mean softmax cross-entropy over the batch of labels[b] in [0, nc) (not
+ * checked on the device): *loss (one device float) and its gradient with
+ * respect to every parameter into grads (same layout as params).  Fixed-order
+ * sums: deterministic.  Async. */
+spmv_status spmv_mlp_grad(const spmv_mlp *net, const float *X, const int32_t *labels,
+                          int32_t batch, float *grads, float *loss, void *work, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected for step
+ * `step` >= 1) on the parameters with moment buffers m, v (device, zeroed
+ * before step 1).  Async. */
+spmv_status spmv_mlp_adam(const spmv_mlp *net, const float *grads, float *m, float *v,
+                          int32_t step, float lr, void *stream);
 
 /* Autotuner (not in the paper; the shapes the paper leaves to OSKI are picked
  * by measurement here): build one plan per candidate option set for the same

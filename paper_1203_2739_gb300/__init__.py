@@ -48,7 +48,9 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
            "spmv_form_from_labels", "spmv_partition", "spmv_partition_free",
            "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
-           "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched")
+           "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched", "spmv_features",
+           "spmv_mlp_param_count", "spmv_mlp_work_bytes", "spmv_mlp_forward", "spmv_mlp_grad",
+           "spmv_mlp_adam")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
@@ -116,6 +118,14 @@ class spmv_partition_out(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class spmv_mlp(ctypes.Structure):
+    _fields_ = [("nin", ctypes.c_int32), ("nh", ctypes.c_int32), ("nc", ctypes.c_int32),
+                ("params", ctypes.c_void_p)]
+
+
+SPMV_SEL_FEATURES = 16
+
+
 class spmv_cg_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32)]
@@ -139,6 +149,15 @@ def _load():
     L.spmv_exec.argtypes = [vp, vp, vp, vp]
     L.spmv_exec_host.argtypes = [vp, vp, vp, vp]
     L.spmv_plan_check.argtypes = [vp, vp]
+    L.spmv_features.argtypes = [ctypes.POINTER(spmv_csr), ctypes.POINTER(ctypes.c_float)]
+    L.spmv_mlp_param_count.argtypes = [ctypes.c_int32] * 3
+    L.spmv_mlp_param_count.restype = ctypes.c_int64
+    L.spmv_mlp_work_bytes.argtypes = [ctypes.c_int32] * 3
+    L.spmv_mlp_work_bytes.restype = ctypes.c_size_t
+    L.spmv_mlp_forward.argtypes = [ctypes.POINTER(spmv_mlp), vp, ctypes.c_int32, vp, vp, vp]
+    L.spmv_mlp_grad.argtypes = [ctypes.POINTER(spmv_mlp), vp, vp, ctypes.c_int32, vp, vp, vp, vp]
+    L.spmv_mlp_adam.argtypes = [ctypes.POINTER(spmv_mlp), vp, vp, vp, ctypes.c_int32,
+                                ctypes.c_float, vp]
     L.spmv_plan_create_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(spmv_csr),
                                            ctypes.POINTER(spmv_perm), ctypes.POINTER(spmv_splits),
                                            ctypes.POINTER(spmv_opts), ctypes.POINTER(vp)]
@@ -166,7 +185,8 @@ def _load():
                  "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
                  "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
                  "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir",
-                 "spmv_plan_create_batched"):
+                 "spmv_plan_create_batched", "spmv_features", "spmv_mlp_forward",
+                 "spmv_mlp_grad", "spmv_mlp_adam"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -408,6 +428,59 @@ def spmv_cg_ir(low, f64, b, x, tol=0.0, inner_tol=0.0, max_outer=0, max_inner=0,
                           ctypes.c_void_p(_stream_handle(stream))))
     return {"outer": info.outer, "inner_total": info.inner_total,
             "rel_residual": info.rel_residual, "converged": bool(info.converged)}
+
+
+def spmv_features(m, n, rowptr, colidx):
+    """The selector's SPMV_SEL_FEATURES features of a CSR matrix (host)."""
+    A, keep = _csr_struct(m, n, rowptr, colidx, None)
+    out = (ctypes.c_float * SPMV_SEL_FEATURES)()
+    _check(lib.spmv_features(ctypes.byref(A), out))
+    return np.array(out[:], dtype=np.float32)
+
+
+def spmv_mlp_param_count(nin, nh, nc):
+    return int(lib.spmv_mlp_param_count(nin, nh, nc))
+
+
+def spmv_mlp_work_bytes(nh, nc, batch):
+    return int(lib.spmv_mlp_work_bytes(nh, nc, batch))
+
+
+def _net(params, nin, nh, nc):
+    torch = _torch()
+    if (not params.is_cuda or params.dtype != torch.float32 or not params.is_contiguous()
+            or params.numel() != spmv_mlp_param_count(nin, nh, nc)):
+        raise ValueError("params must be a contiguous CUDA float32 tensor of "
+                         "spmv_mlp_param_count(nin, nh, nc) entries")
+    return spmv_mlp(nin, nh, nc, params.data_ptr())
+
+
+def spmv_mlp_forward(params, nin, nh, nc, X, logits, work, stream=None):
+    """logits (batch x nc) = net(X); float32 CUDA tensors; work: a CUDA byte
+    tensor of at least spmv_mlp_work_bytes(nh, nc, batch)."""
+    net = _net(params, nin, nh, nc)
+    _check(lib.spmv_mlp_forward(ctypes.byref(net), ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                ctypes.c_void_p(logits.data_ptr()),
+                                ctypes.c_void_p(work.data_ptr()),
+                                ctypes.c_void_p(_stream_handle(stream))))
+
+
+def spmv_mlp_grad(params, nin, nh, nc, X, labels, grads, loss, work, stream=None):
+    """Gradient of the mean softmax cross-entropy into grads (like params) and
+    the loss into loss (one float); labels: int32 CUDA tensor."""
+    net = _net(params, nin, nh, nc)
+    _check(lib.spmv_mlp_grad(ctypes.byref(net), ctypes.c_void_p(X.data_ptr()),
+                             ctypes.c_void_p(labels.data_ptr()), X.shape[0],
+                             ctypes.c_void_p(grads.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                             ctypes.c_void_p(work.data_ptr()),
+                             ctypes.c_void_p(_stream_handle(stream))))
+
+
+def spmv_mlp_adam(params, nin, nh, nc, grads, m, v, step, lr, stream=None):
+    net = _net(params, nin, nh, nc)
+    _check(lib.spmv_mlp_adam(ctypes.byref(net), ctypes.c_void_p(grads.data_ptr()),
+                             ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                             int(step), float(lr), ctypes.c_void_p(_stream_handle(stream))))
 
 
 def _host_ptr(a, rows, plan, what):

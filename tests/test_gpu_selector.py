@@ -1,0 +1,108 @@
+"""The selector network's CUDA kernels through the C ABI: forward pass and
+gradients against the CPU oracle's FP64 network (itself pinned by finite
+differences), the Adam step against its textbook update, and training on a
+labelled problem the network must learn."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+S = None
+SEL = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global S, SEL
+    import paper_1203_2739_gb300 as lib
+    import paper_1203_2739_gb300.selector as sel
+    S, SEL = lib, sel
+    torch.cuda.set_device(0)
+    yield
+
+
+def _random_net(rng, nin, nh, nc):
+    shapes = [(nh, nin), (nh,), (nh, nh), (nh,), (nc, nh), (nc,)]
+    parts = [rng.normal(0, 0.4, s) for s in shapes]
+    flat = np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+    return parts, flat
+
+
+def _split(flat, nin, nh, nc):
+    sizes = [nh * nin, nh, nh * nh, nh, nc * nh, nc]
+    out, o = [], 0
+    for k in sizes:
+        out.append(flat[o:o + k])
+        o += k
+    return out
+
+
+@pytest.mark.parametrize("nin,nh,nc,batch", [(16, 64, 13, 37), (5, 8, 3, 1), (16, 64, 13, 300)])
+def test_forward_and_gradients_match_oracle(nin, nh, nc, batch):
+    rng = np.random.default_rng(nin + nh + batch)
+    parts, flat = _random_net(rng, nin, nh, nc)
+    # the oracle computes with the FP32-rounded parameters and inputs
+    parts64 = [p.astype(np.float32).astype(np.float64) for p in parts]
+    X = rng.normal(0, 1, (batch, nin)).astype(np.float32)
+    y = rng.integers(0, nc, batch).astype(np.int32)
+    loss_ref, logits_ref, grads_ref = oracle.mlp_loss_grad(X.astype(np.float64), y, parts64)
+
+    P = torch.from_numpy(flat).cuda()
+    Xd = torch.from_numpy(X).cuda()
+    work = torch.empty(S.spmv_mlp_work_bytes(nh, nc, batch), dtype=torch.uint8, device="cuda")
+    logits = torch.empty(batch, nc, device="cuda")
+    S.spmv_mlp_forward(P, nin, nh, nc, Xd, logits, work)
+    g = torch.empty_like(P)
+    loss = torch.zeros(1, device="cuda")
+    S.spmv_mlp_grad(P, nin, nh, nc, Xd, torch.from_numpy(y).cuda(), g, loss, work)
+    torch.cuda.synchronize()
+    assert np.allclose(logits.cpu().numpy(), logits_ref, rtol=1e-5, atol=1e-5)
+    assert abs(loss.item() - loss_ref) <= 1e-5 * max(1.0, loss_ref)
+    for got, want in zip(_split(g.cpu().numpy(), nin, nh, nc), grads_ref):
+        want = want.reshape(-1)
+        scale = max(1e-3, np.abs(want).max())
+        assert np.abs(got - want).max() <= 1e-4 * scale
+
+
+def test_adam_step_matches_its_definition():
+    rng = np.random.default_rng(3)
+    nin, nh, nc = 4, 6, 3
+    _, flat = _random_net(rng, nin, nh, nc)
+    g = rng.normal(0, 1, flat.size).astype(np.float32)
+    m0 = rng.normal(0, 0.1, flat.size).astype(np.float32)
+    v0 = np.abs(rng.normal(0, 0.1, flat.size)).astype(np.float32)
+    P, G = torch.from_numpy(flat.copy()).cuda(), torch.from_numpy(g).cuda()
+    M, V = torch.from_numpy(m0.copy()).cuda(), torch.from_numpy(v0.copy()).cuda()
+    step, lr = 7, 1e-2
+    S.spmv_mlp_adam(P, nin, nh, nc, G, M, V, step, lr)
+    torch.cuda.synchronize()
+    m1 = 0.9 * m0.astype(np.float64) + 0.1 * g
+    v1 = 0.999 * v0.astype(np.float64) + 0.001 * g.astype(np.float64) ** 2
+    p1 = flat - lr * (m1 / (1 - 0.9 ** step)) / (np.sqrt(v1 / (1 - 0.999 ** step)) + 1e-8)
+    assert np.allclose(M.cpu().numpy(), m1, rtol=1e-5, atol=1e-7)
+    assert np.allclose(V.cpu().numpy(), v1, rtol=1e-5, atol=1e-8)
+    assert np.allclose(P.cpu().numpy(), p1, rtol=1e-5, atol=1e-6)
+
+
+def test_training_learns_a_labelled_problem():
+    # the class is the argmax of a fixed random linear map of the features:
+    # learnable by the network, far from chance before training
+    rng = np.random.default_rng(11)
+    nc = len(SEL.CLASSES)
+    Wt = rng.normal(0, 1, (nc, 16))
+    F = rng.normal(0, 1, (4500, 16)).astype(np.float32)
+    lab = (F @ Wt.T).argmax(axis=1)
+    sel = SEL.Selector(seed=1)
+    before = (sel.proba(F[4000:]).argmax(axis=1) == lab[4000:]).mean()
+    hist = sel.fit(F[:4000], lab[:4000], epochs=40, lr=3e-3, batch=200)
+    after = (sel.proba(F[4000:]).argmax(axis=1) == lab[4000:]).mean()
+    # (the same training in FP64 on the CPU oracle's gradients reaches 0.90)
+    assert hist[-1] < 0.2 * hist[0]
+    assert after >= 0.82 and after > before + 0.5
+    # confidence-gated choice: -1 (time every class) only below the threshold
+    p = sel.proba(F[4000:])
+    ch = sel.choose(F[4000:], min_confidence=0.9)
+    assert np.all((ch == -1) == (p.max(axis=1) < 0.9))

@@ -112,10 +112,11 @@ def test_sb_mesh_exact_and_staged(K):
                                form=S.SPMV_SB, K=K, row_part_ptr=rpp, col_part_ptr=cpp,
                                tile_cols=1024, dtype=dtype, flags=S.SPMV_FLAG_STAGE)
         _check(p, m, n, rp, ci, vi, synth.integer_x(n, 3), exact=True)
+        # default 256-thread CTAs stage nothing
         p = S.spmv_plan_create(m, n, rp, ci, vi, row_perm=rperm, col_perm=cperm,
                                form=S.SPMV_SB, K=K, row_part_ptr=rpp, col_part_ptr=cpp,
                                dtype=dtype)
-        assert p.info["n_staged_tiles"] == 0      # default: 256-thread CTAs stage nothing
+        assert p.info["n_staged_tiles"] == 0
         _check(p, m, n, rp, ci, vi, synth.integer_x(n, 3), exact=True)
 
 
