@@ -79,12 +79,9 @@ enum {
                                     default is one CTA per tile, with tiles
                                     sized so that they fill about one wave of
                                     resident CTAs */
-    SPMV_FLAG_STAGE = 16         /* stage x in 256-thread CTAs too (every
-                                    column of a tile when they fit, with
-                                    16-bit indices; else the entries that pay);
-                                    by default only wide 1024-thread CTAs
-                                    stage, where the window is large enough
-                                    to pay on GB300 */
+    SPMV_FLAG_STAGE = 16         /* stage x in 256-thread CTAs too; by default
+                                    only wide (1024-thread) CTAs stage, where
+                                    the window is large enough to pay */
 };
 
 /* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,

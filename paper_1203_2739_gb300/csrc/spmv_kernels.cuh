@@ -52,6 +52,10 @@ constexpr int kWideThreads = 1024;
 #ifndef SPMV_TILE_MINBLOCKS
 #define SPMV_TILE_MINBLOCKS 6
 #endif
+//   SPMV_WIDE_U       elements per lane in flight per batch in the wide CTAs
+#ifndef SPMV_WIDE_U
+#define SPMV_WIDE_U 8
+#endif
 //   SPMV_L1_PREF      1 = ask for the largest L1 carveout for the tile kernels
 #ifndef SPMV_L1_PREF
 #define SPMV_L1_PREF 0
@@ -331,7 +335,9 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
             for (int c = 0; c < R; ++c) partial[ps + c] = s[c];
         }
     };
-    constexpr int U = R == 1 ? 8 : (R == 2 ? 4 : 2);
+    // elements per lane in flight per batch (the wide CTAs have the larger
+    // register budget)
+    constexpr int U = (R == 1 ? (NT == kThreads ? 8 : SPMV_WIDE_U) : (R == 2 ? 4 : 2));
 
     // rows too long for one lane: a warp each, batches of U loads per lane
     for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += NT / 32) {

@@ -215,7 +215,6 @@ struct TileCfg {
     int32_t entry_bytes;  // bytes of one x entry (r values)
     int32_t list_min;   // uses in the tile that put a column outside the run on the list
     bool stage;         // staging allowed
-    bool narrow_only;   // stage only tiles whose every column fits (NARROW)
 };
 
 // Cuts the plan rows of the parts into tiles of consecutive rows with a
@@ -306,39 +305,18 @@ struct Tiler {
             const double b_cost = (double)multi.size();
             const double a_gain = a_fits ? (double)a_saved - a_cost : -1.0;
             const double b_gain = (double)b_saved - b_cost;
-            // option (c): every column the tile uses -- the run over its home
-            // columns and all others on the list -- when they all fit; the
-            // tile then reads x only from shared memory and stores 16-bit
-            // column indices (10 bytes per FP64 nonzero instead of 12)
-            int64_t c_list = 0;
-            for (int32_t c : used)
-                if (!(runlen > 0 && c >= run0 && c < run0 + runlen)) ++c_list;
-            const bool c_fits = runlen + c_list <= cfg.W;
-            const bool use_c = c_fits;
-            const bool use_a = !use_c && a_fits && a_gain >= b_gain;
+            const bool use_a = a_fits && a_gain >= b_gain;
             const double gain = use_a ? a_gain : b_gain;
             const double cost = use_a ? a_cost : b_cost;
             // stage when it saves at least as many requests as it costs: a
             // staged entry is fetched before the tile's rows start, where its
-            // latency is not hidden (tiles that can stage every column always
-            // do; with narrow_only, only those stage)
-            const bool stage_it = use_c || (!cfg.narrow_only && gain > 0.0 && gain >= cost);
-            if (stage_it) {
-                if (!use_a && !use_c) run0 = runlen = 0;
+            // latency is not hidden
+            if (gain > 0.0 && gain >= cost) {
+                if (!use_a) run0 = runlen = 0;
                 int32_t pos = runlen, listlen = 0, direct = 0;
                 t.list0 = (int32_t)P.xlist.size();
                 for (int32_t c : used) loc[c] = -1;
-                if (use_c) {
-                    for (int32_t c : used) {
-                        if (runlen > 0 && c >= run0 && c < run0 + runlen) {
-                            loc[c] = c - run0;
-                        } else {
-                            loc[c] = pos++;
-                            P.xlist.push_back(c);
-                            ++listlen;
-                        }
-                    }
-                } else if (use_a) {
+                if (use_a) {
                     for (int32_t c : used) {
                         if (c >= run0 && c < run0 + runlen) loc[c] = c - run0;
                         else if (cnt[c] >= cfg.list_min) {
@@ -384,12 +362,18 @@ struct Tiler {
         };
         order.clear();
         t.vrow0 = (int32_t)P.vrows.size();
+        // the warp rows longest first: the warps take them round-robin, so
+        // this keeps the warps of the CTA about equally busy
+        std::vector<int32_t> wide_rows;
         for (int32_t r : rows) {
+            if (prp[r + 1] - prp[r] <= cfg.vrow_len) order.push_back(r);
+            else wide_rows.push_back(r);
+        }
+        std::stable_sort(wide_rows.begin(), wide_rows.end(), [&](int32_t a, int32_t b) {
+            return prp[a + 1] - prp[a] > prp[b + 1] - prp[b];
+        });
+        for (int32_t r : wide_rows) {
             const int32_t a = prp[r], len = prp[r + 1] - a;
-            if (len <= cfg.vrow_len) {
-                order.push_back(r);
-                continue;
-            }
             const size_t e0 = P.val.size();
             P.val.resize(e0 + len, 0.0);
             P.col32.resize(e0 + len, 0);
@@ -723,7 +707,6 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         cfg.long_t = o.long_row > 0 ? o.long_row : std::max<int32_t>(1024, cfg.tnnz / 4);
     }
     cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING) && (wide || (o.flags & SPMV_FLAG_STAGE));
-    cfg.narrow_only = false;
     P->lanes = 32;                 // one lane per row, 32 rows per chunk
     P->long_thresh = cfg.long_t;
 
