@@ -815,6 +815,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "selector" and args.impl == "reference":
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the selector workload measures choices among this "
+                                         "library's own plans; it has no CPU reference arm"}))
+        return
     if args.workload == "selector":
         # partitions on host processes started before any GPU work
         import multiprocessing as mp
