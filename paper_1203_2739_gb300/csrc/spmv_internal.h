@@ -18,8 +18,9 @@ void clear_error();
 // ----------------------------------------------------------------- tiles --
 // A tile is the unit of work of one CTA in the tiled kernel.  It plays the
 // part the paper gives to a submatrix that "fits into the cache" (Sec. 3):
-// the x entries it reuses are staged once in the CTA's shared memory; the
-// ones it touches only once are gathered straight from L2.
+// when the plan stages, the x entries it reuses are copied once into the
+// CTA's shared memory and the others are gathered through L1 / L2; otherwise
+// every x entry is gathered.
 //
 // Inside a tile the rows are sorted by length and cut into chunks of 32; a
 // chunk is stored column-major (element k of the chunk's 32 rows are 32

@@ -7,17 +7,21 @@
 //                     (evict-first), x gathered through the read-only path,
 //                     warp-shuffle reduction; rows longer than a threshold get
 //                     a whole CTA each.  This is the baseline.
-//  * k_tiles       -- one CTA per tile of a part of the SB / DB form or of a
-//                     split (Sec. 3, Sec. 4).  The tile first copies the x
-//                     entries it reuses into shared memory -- the "cache" the
-//                     partition was sized for -- then each warp takes chunks of
-//                     32 length-sorted rows stored column-major: one lane per
-//                     row, coalesced loads, one FMA chain per row.  No FP64
-//                     instruction runs with idle lanes for want of work and no
-//                     shuffle reduction is needed, which matters on GB300 where
-//                     FP64 issues at two FMAs per SM per clock.  Columns used
-//                     once by the tile are gathered from L2 directly.  Chunk
-//                     tiles reduce a slice of one long row into a partial sum.
+//  * k_tiles       -- one CTA per tile of consecutive rows of the SB / DB
+//                     form or of a split (Sec. 3, Sec. 4).  When the plan says
+//                     so, the tile first copies the x window it reuses into
+//                     shared memory -- the "cache" the partition was sized
+//                     for -- with one bulk copy for the contiguous run of home
+//                     columns and a gather for the listed others.  Then each
+//                     warp takes chunks of 32 length-sorted rows stored
+//                     column-major: one lane per row, coalesced loads, one FMA
+//                     chain per row.  No FP64 instruction runs with idle lanes
+//                     for want of work and no shuffle reduction is needed,
+//                     which matters on GB300 where FP64 issues at two FMAs per
+//                     SM per clock.  Columns not staged are gathered through
+//                     L1 / L2.  Chunk tiles reduce a slice of one long row
+//                     into a partial sum.  256-thread CTAs (several per SM)
+//                     or 1024-thread CTAs (one per SM, large windows).
 //  * k_fixup       -- rows with several contributions (split rows shared by
 //                     parts, chunked long rows) are summed from their partial
 //                     sums in part order: y <- y + A^k x accumulated on the fly
