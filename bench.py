@@ -402,10 +402,12 @@ def run_ours(args, rank, world, local_rank):
             kw, pres = form_kwargs(S, f, rp, ci, parts)
             t1 = time.perf_counter()
             chosen = None
-            # tile shapes: one wave of 256-thread tiles (staging nothing, or
-            # staging x), wide tiles, or eight waves of smaller tiles (launched in order, so that the x windows of the
+            # tile shapes: one wave of 256-thread tiles (rows over 64 or over
+            # 128 nonzeros reduced by a warp; or staging x), wide tiles, or
+            # eight waves of smaller tiles (launched in order, so that the x windows of the
             # tiles running at once stay within L2 when x does not)
             shapes = {"cta256": dict(dtype=dtype),
+                      "cta256w": dict(dtype=dtype, warp_rows=128),
                       "cta256s": dict(dtype=dtype, flags=S.SPMV_FLAG_STAGE),
                       "cta1024": dict(dtype=dtype, cta_threads=1024),
                       "cta256x8": dict(dtype=dtype,
@@ -812,7 +814,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="tiled forms with the default tile shape instead of the autotuned one")
-    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256s", "cta1024",
+    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256w", "cta256s", "cta1024",
                                                     "cta256x8"],
                     help="tiled forms with this tile shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,

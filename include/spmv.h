@@ -134,6 +134,9 @@ typedef struct spmv_opts {
     int32_t lanes;        /* threads cooperating on one row: 2, 4, 8, 16 or 32
                              (0 = chosen from the mean row length) */
     int32_t flags;        /* SPMV_FLAG_* */
+    int32_t warp_rows;    /* tiled forms: rows longer than this are reduced
+                             by a whole warp, shorter ones go into the chunks
+                             of 32 rows (0 = 64) */
     int32_t cta_threads;  /* tiled forms: 256 = several CTAs per SM, tiles
                              for one wave of them, x through L1/L2 (0 = this);
                              1024 = one wide CTA per SM, tiles for four waves,

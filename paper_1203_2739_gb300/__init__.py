@@ -84,7 +84,8 @@ class spmv_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("tile_cols", ctypes.c_int32), ("tile_nnz", ctypes.c_int32),
                 ("long_row", ctypes.c_int32), ("lanes", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("warp_rows", ctypes.c_int32),
+                ("cta_threads", ctypes.c_int32),
                 ("alloc", _ALLOC_T), ("release", _FREE_T),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -277,7 +278,8 @@ class Plan:
 def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
                      form=SPMV_NATURAL, K=0, row_part_ptr=None, col_part_ptr=None,
                      nz_part=None, dtype=SPMV_F64, nrhs=1, tile_cols=0, tile_nnz=0,
-                     long_row=0, lanes=0, flags=0, cta_threads=0, allocator="torch"):
+                     long_row=0, lanes=0, flags=0, cta_threads=0, warp_rows=0,
+                     allocator="torch"):
     A, keep = _csr_struct(m, n, rowptr, colidx, vals)
     rperm = None if row_perm is None else _i32(row_perm)
     cperm = None if col_perm is None else _i32(col_perm)
@@ -286,7 +288,8 @@ def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
     cpp = None if col_part_ptr is None else _i32(col_part_ptr)
     nzp = None if nz_part is None else _i32(nz_part)
     splits = spmv_splits(form, K, _ptr(rpp), _ptr(cpp), _ptr(nzp))
-    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, cta_threads)
+    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, warp_rows,
+                     cta_threads)
     if allocator == "torch":
         opts.alloc, opts.release = _ALLOC_CB, _FREE_CB
     handle = ctypes.c_void_p()
@@ -299,7 +302,7 @@ def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
 
 def spmv_plan_create_batched(mats, perms=None, nz_parts=None, K=0, dtype=SPMV_F64, nrhs=1,
                              tile_cols=0, tile_nnz=0, long_row=0, lanes=0, flags=0,
-                             cta_threads=0, allocator="torch"):
+                             cta_threads=0, warp_rows=0, allocator="torch"):
     """One plan over the block-diagonal matrix of `mats` (a list of
     (m, n, rowptr, colidx, vals)); perms: None or a list of (row_perm,
     col_perm) pairs (None members = identity); nz_parts: None (natural form)
@@ -327,7 +330,8 @@ def spmv_plan_create_batched(mats, perms=None, nz_parts=None, K=0, dtype=SPMV_F6
             nzp = _i32(lab)
             keep.append(nzp)
             sp[b] = spmv_splits(SPMV_SPLIT, K, None, None, _ptr(nzp))
-    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, cta_threads)
+    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, warp_rows,
+                     cta_threads)
     if allocator == "torch":
         opts.alloc, opts.release = _ALLOC_CB, _FREE_CB
     handle = ctypes.c_void_p()
@@ -356,7 +360,7 @@ def spmv_plan_autotune(m, n, rowptr, colidx, vals, candidates, reps=5, stream=No
     for i, c in enumerate(candidates):
         o = arr[i]
         for k in ("dtype", "nrhs", "tile_cols", "tile_nnz", "long_row", "lanes", "flags",
-                  "cta_threads"):
+                  "warp_rows", "cta_threads"):
             setattr(o, k, int(c.get(k, 0)))
         if allocator == "torch":
             o.alloc, o.release = _ALLOC_CB, _FREE_CB

@@ -486,6 +486,10 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         set_error("nrhs=%d: supported right-hand-side counts are 1, 2, 4, 8", o.nrhs);
         return SPMV_E_UNSUPPORTED;
     }
+    if (o.warp_rows < 0) {
+        set_error("warp_rows=%d must be >= 0", o.warp_rows);
+        return SPMV_E_INVALID;
+    }
     if (o.lanes != 0 && o.lanes != 1 && o.lanes != 2 && o.lanes != 4 && o.lanes != 8 &&
         o.lanes != 16 && o.lanes != 32) {
         set_error("lanes=%d: must be 0, 1, 2, 4, 8, 16 or 32", o.lanes);
@@ -692,7 +696,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     cfg.align = std::max(1, 16 / (xb * r));
     cfg.list_min = 3;
     cfg.max_rows = 4096;
-    cfg.vrow_len = 64;
+    cfg.vrow_len = o.warp_rows > 0 ? o.warp_rows : 64;
     // tiles sized so that one launch is about one wave of resident CTAs
     // (ctas_per_sm per SM): every CTA starts at once and none waits for
     // a slot, so there is no tail wave.  Rows longer than long_t are cut into

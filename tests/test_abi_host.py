@@ -83,6 +83,8 @@ def test_plan_create_validation_before_any_device_call():
     assert _plan_status(lanes=3)[0] == S.SPMV_E_INVALID
     assert _plan_status(dtype=7)[0] == S.SPMV_E_INVALID
     assert _plan_status(tile_cols=1 << 20)[0] == S.SPMV_E_UNSUPPORTED
+    st, msg = _plan_status(warp_rows=-1)
+    assert st == S.SPMV_E_INVALID and "warp_rows" in msg
     st, msg = _plan_status(cta_threads=512)
     assert st == S.SPMV_E_INVALID and "cta_threads" in msg
     st, msg = _plan_status(cta_threads=1024, flags=S.SPMV_FLAG_PERSISTENT | 2)

@@ -211,6 +211,17 @@ def test_wide_ctas_staged_mesh():
     _check(plan, m, n, rp, ci, vi, synth.integer_x(n, 36), exact=True)
 
 
+@pytest.mark.parametrize("warp_rows", [8, 128, 600])
+def test_warp_row_threshold_exact(zipf, warp_rows):
+    m, n, rp, ci, _ = zipf
+    vi = synth.integer_values(int(rp[-1]), 44)
+    for plan in (_sb_plan(m, n, rp, ci, vi, 8, 45, warp_rows=warp_rows),
+                 _split_plan(m, n, rp, ci, vi, 16, 46, warp_rows=warp_rows, nrhs=2)):
+        x = synth.integer_x(n, 47, nrhs=plan.info["nrhs"])
+        _check(plan, m, n, rp, ci, vi, x if plan.info["nrhs"] > 1 else x.reshape(-1),
+               exact=True)
+
+
 def test_autotune_keeps_a_correct_plan(zipf):
     m, n, rp, ci, _ = zipf
     vi = synth.integer_values(int(rp[-1]), 41)
