@@ -205,7 +205,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -260,20 +260,24 @@ def kernel_name(info, dtype):
     return "k_tiles<%d, %s, %s, %d>" % (r, vt, xt, nt)
 
 
+KERNEL_SOURCES = ("spmv_kernels.cuh", "spmv_kern_f64.cu", "spmv_kern_f32.cu", "spmv_kern_bf16.cu",
+                  "spmv_device.h", "spmv_internal.h", "spmv_plan.cpp", "spmv_capi.cu")
+
+
 def kernel_source_hash():
-    """Hash of the library's sources with comments and blank space removed,
-    so that the record of an ncu capture survives edits to comments only."""
+    """Hash of the sources of the SpMV kernels and of the plans they run
+    (the layout of every tile), with comments and blank space removed, so
+    that the record of an ncu capture survives edits to comments only."""
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1203_2739_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
-                text = fh.read()
-            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            text = re.sub(r"//[^\n]*", "", text)
-            h.update(f.encode())
-            h.update("".join(text.split()).encode())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(f.encode())
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
@@ -799,7 +803,7 @@ def run_selector(args, pool_results):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=sorted(MATRICES) + ["selector"])

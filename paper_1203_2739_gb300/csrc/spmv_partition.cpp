@@ -344,10 +344,13 @@ struct GainHeap {
     const std::vector<i64> *gain;
     const std::vector<uint32_t> *tb;
 
+    // a strict total order, so the top does not depend on the heap's layout
     bool above(i32 a, i32 b) const
     {
         const i64 ga = (*gain)[a], gb = (*gain)[b];
-        return ga > gb || (ga == gb && (*tb)[a] > (*tb)[b]);
+        if (ga != gb) return ga > gb;
+        const uint32_t ta = (*tb)[a], tbb = (*tb)[b];
+        return ta != tbb ? ta > tbb : a < b;
     }
     void up(size_t i)
     {
@@ -461,19 +464,43 @@ struct FM {
 
     std::vector<i32> pending;        // vertices entering the candidate set
     std::vector<uint8_t> is_pending;
+    // gain changes of one move, summed per vertex before the heaps see them
+    // (at coarse levels a move touches the same few vertices through
+    // thousands of nets)
+    std::vector<i64> delta;
+    std::vector<i32> touched;
+    std::vector<uint8_t> is_touched;
 
     void bump(i32 u, i64 d)
     {
         if (locked[u]) return;
-        if (pos[u] >= 0) {
-            gain[u] += d;
-            heap[side[u]].update(u);
-        } else if (!is_pending[u]) {
-            // not a candidate yet: its exact gain is computed once the move
-            // is complete
-            is_pending[u] = 1;
-            pending.push_back(u);
+        if (!is_touched[u]) {
+            is_touched[u] = 1;
+            touched.push_back(u);
         }
+        delta[u] += d;
+    }
+
+    void flush_bumps()
+    {
+        for (i32 u : touched) {
+            is_touched[u] = 0;
+            const i64 d = delta[u];
+            delta[u] = 0;
+            if (locked[u]) continue;
+            if (pos[u] >= 0) {
+                if (d != 0) {
+                    gain[u] += d;
+                    heap[side[u]].update(u);
+                }
+            } else if (!is_pending[u]) {
+                // not a candidate yet: its exact gain is computed once the
+                // move is complete
+                is_pending[u] = 1;
+                pending.push_back(u);
+            }
+        }
+        touched.clear();
     }
 
     void flush_pending()
@@ -495,6 +522,9 @@ struct FM {
         pos.assign((size_t)G.nv, -1);
         tb.resize((size_t)G.nv);
         is_pending.assign((size_t)G.nv, 0);
+        delta.assign((size_t)G.nv, 0);
+        is_touched.assign((size_t)G.nv, 0);
+        touched.clear();
         i64 total = 0;
         for (int pass = 0; pass < passes; ++pass) {
             locked.assign((size_t)G.nv, 0);
@@ -621,6 +651,7 @@ struct FM {
         w[s] -= G.vw[v];
         w[t] += G.vw[v];
         side[v] = (uint8_t)t;
+        flush_bumps();
     }
 };
 
@@ -650,6 +681,8 @@ void grow(const HG &G, i64 target0, std::mt19937_64 &rng, std::vector<uint8_t> &
     fm.pos.assign((size_t)G.nv, -1);
     fm.tb.resize((size_t)G.nv);
     fm.is_pending.assign((size_t)G.nv, 0);
+    fm.delta.assign((size_t)G.nv, 0);
+    fm.is_touched.assign((size_t)G.nv, 0);
     fm.locked.assign((size_t)G.nv, 0);
     for (i32 v = 0; v < G.nv; ++v) {
         fm.tb[v] = (uint32_t)rng();
