@@ -300,8 +300,9 @@ size_t spmv_mlp_work_bytes(int32_t nh, int32_t nc, int32_t batch);
 spmv_status spmv_mlp_forward(const spmv_mlp *net, const float *X, int32_t batch,
                              float *logits, void *work, void *stream);
 
-/* Mean softmax cross-entropy over the batch of labels[b] in [0, nc) (not
- * checked on the device): *loss (one device float) and its gradient with
+/* Mean softmax cross-entropy over the batch of labels[b] in [0, nc) (a
+ * label outside that range makes *loss NaN and contributes no gradient):
+ * *loss (one device float) and its gradient with
  * respect to every parameter into grads (same layout as params).  Fixed-order
  * sums: deterministic.  Async. */
 spmv_status spmv_mlp_grad(const spmv_mlp *net, const float *X, const int32_t *labels,

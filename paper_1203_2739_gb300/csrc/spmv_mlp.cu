@@ -66,6 +66,12 @@ __global__ void k_softmax_xent(const float *__restrict__ Z, const int32_t *__res
     for (int32_t o = 0; o < nc; ++o) se += expf(z[o] - zmax);
     const float lse = zmax + logf(se);
     const int32_t y = labels[b];
+    if (y < 0 || y >= nc) {
+        // a label outside [0, nc): no gradient, and the loss says so (NaN)
+        sample_loss[b] = __int_as_float(0x7fc00000);
+        for (int32_t o = 0; o < nc; ++o) dZ[(int64_t)b * nc + o] = 0.0f;
+        return;
+    }
     sample_loss[b] = lse - z[y];
     for (int32_t o = 0; o < nc; ++o)
         dZ[(int64_t)b * nc + o] = (expf(z[o] - lse) - (o == y ? 1.0f : 0.0f)) / (float)batch;

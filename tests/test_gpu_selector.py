@@ -106,3 +106,20 @@ def test_training_learns_a_labelled_problem():
     p = sel.proba(F[4000:])
     ch = sel.choose(F[4000:], min_confidence=0.9)
     assert np.all((ch == -1) == (p.max(axis=1) < 0.9))
+
+
+def test_out_of_range_label_gives_nan_loss_not_a_fault():
+    rng = np.random.default_rng(9)
+    nin, nh, nc, batch = 4, 8, 3, 5
+    _, flat = _random_net(rng, nin, nh, nc)
+    P = torch.from_numpy(flat).cuda()
+    X = torch.from_numpy(rng.normal(0, 1, (batch, nin)).astype(np.float32)).cuda()
+    y = torch.tensor([0, 1, 7, 2, -1], dtype=torch.int32, device="cuda")
+    work = torch.empty(S.spmv_mlp_work_bytes(nh, nc, batch), dtype=torch.uint8, device="cuda")
+    g = torch.empty_like(P)
+    loss = torch.zeros(1, device="cuda")
+    S.spmv_mlp_grad(P, nin, nh, nc, X, y, g, loss, work)
+    torch.cuda.synchronize()
+    assert np.isnan(loss.item())
+    assert np.all(np.isfinite(g.cpu().numpy()))
+
