@@ -157,3 +157,83 @@ def test_row_segments_on_large_matrices():
     for method in (S.SPMV_PART_RCN, S.SPMV_PART_ERCN):
         res = S.spmv_partition(m, n, rp, ci, method, K=16, seed=1)
         assert res["cost"] == _bound(res, m, n, rp, ci)
+
+
+def _balance_limits(w, eps=0.10):
+    """The bisection's balance rule: a side may hold up to (1 + eps) of half
+    the total vertex weight, and never less than half plus the heaviest
+    vertex (so that a feasible split always exists)."""
+    import math
+    total = int(w.sum())
+    half = total // 2
+    maxw = math.ceil((1.0 + eps) * total / 2.0)
+    vmax = int(w.max())
+    return max(maxw, half + vmax), max(maxw, total - half + vmax)
+
+
+def _all_sides(nv):
+    return ((np.arange(1 << nv)[:, None] >> np.arange(nv)[None, :]) & 1).astype(np.int64)
+
+
+def _tiny_cn_case(seed):
+    """Best balanced column-net bisection of a random matrix of at most 12
+    rows by enumeration, and the partitioner's K = 2 result."""
+    rng = np.random.default_rng(seed)
+    m, n = int(rng.integers(6, 13)), int(rng.integers(5, 16))
+    rp, ci, _ = synth.random_sparse(m, n, float(rng.uniform(0.15, 0.4)), seed + 100)
+    A = (synth.csr_to_dense(m, n, rp, ci, np.ones(ci.size)) != 0).astype(np.int64)
+    w = 12 * np.diff(rp).astype(np.int64) + 12           # a row's CSR bytes
+    mw0, mw1 = _balance_limits(w)
+    B = _all_sides(m)
+    w1 = B @ w
+    ok = ((w.sum() - w1) <= mw0) & (w1 <= mw1)
+    lam = (((1 - B) @ A) > 0).astype(np.int64) + ((B @ A) > 0)
+    best = int(lam.sum(axis=1)[ok].min())
+    res = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_CN, K=2, seed=seed)
+    assert res["cost"] == oracle.bound_sb(m, n, rp, ci, 2, res["labels"])
+    side = res["labels"].astype(np.int64)
+    assert (w[side == 0].sum() <= mw0) and (w[side == 1].sum() <= mw1)
+    return res["cost"], best
+
+
+def _tiny_rcn_case(seed):
+    """Best balanced row-column-net bisection of a random matrix of at most
+    13 nonzeros by enumeration, and the partitioner's K = 2 result."""
+    rng = np.random.default_rng(seed + 50)
+    while True:
+        m, n = int(rng.integers(3, 7)), int(rng.integers(3, 7))
+        rp, ci, _ = synth.random_sparse(m, n, 0.45, int(rng.integers(1 << 30)))
+        if 4 <= ci.size <= 13:
+            break
+    nnz = ci.size
+    rows = np.repeat(np.arange(m), np.diff(rp))
+    w = np.full(nnz, 12, dtype=np.int64)                 # a nonzero's bytes
+    mw0, mw1 = _balance_limits(w)
+    B = _all_sides(nnz)
+    w1 = B @ w
+    ok = ((w.sum() - w1) <= mw0) & (w1 <= mw1)
+    R = np.zeros((nnz, m), dtype=np.int64)
+    R[np.arange(nnz), rows] = 1
+    C = np.zeros((nnz, n), dtype=np.int64)
+    C[np.arange(nnz), ci] = 1
+    cost = sum(((((1 - B) @ M) > 0).astype(np.int64) + ((B @ M) > 0)).sum(axis=1)
+               for M in (R, C))
+    best = int(cost[ok].min())
+    res = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_RCN, K=2, seed=seed)
+    assert res["cost"] == _bound(res, m, n, rp, ci)
+    side = res["labels"].astype(np.int64)
+    assert (w[side == 0].sum() <= mw0) and (w[side == 1].sum() <= mw1)
+    return res["cost"], best
+
+
+@pytest.mark.parametrize("case", [_tiny_cn_case, _tiny_rcn_case])
+def test_bisection_against_enumeration_on_tiny_hypergraphs(case):
+    """K = 2 on 200 tiny matrices against every balanced bisection: the
+    result is balanced and exactly costed, and the multilevel FM heuristic
+    finds the optimum in at least 97% of the cases and is never more than one
+    net piece above it (measured: 199/200 column-net, 198/200
+    row-column-net)."""
+    got = np.array([case(seed) for seed in range(200)])
+    excess = got[:, 0] - got[:, 1]
+    assert excess.min() >= 0
+    assert (excess == 0).mean() >= 0.97 and excess.max() <= 1, excess
