@@ -17,9 +17,15 @@ Metric: compulsory-bytes SpMV throughput, GB/s = sum over the step of
 GFLOP/s = 2 nnz / time and the roofline of the dominant kernel against the
 measured HBM copy bandwidth.
 
+Other workloads: precision (CG with FP64 refinement over FP64 / FP32 / BF16
+products on a 3D Laplacian), batching (256 R-MAT matrices of 1,024-262,144
+rows in one plan, natural vs split K = 16, plus 100 products replayed from a
+CUDA graph), scale (a mesh whose x exceeds L2), zipf16k, selector.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload sweep|zipf16k|precision] [--forms a,b,...]
-                       [--dtype f64|f32|bf16]
+                       [--workload sweep|zipf16k|precision|batching|scale|selector]
+                       [--forms a,b,...] [--dtype f64|f32|bf16] [--nrhs 1|2|4|8]
+                       [--batch-count B] [--batch-max-rows M]
 """
 from __future__ import annotations
 
@@ -47,23 +53,58 @@ MATRICES = {
     "zipf16k": [("zipf16k", lambda: synth.zipf_matrix(seed=0))],
     "precision": [("laplace3d_128", lambda: synth.laplacian3d(128, seed=0))],
     "scale": [("mesh5_6144", lambda: synth.mesh5(6144, seed=0))],
-    "batching": [("rmat_batch64", lambda: _batch_matrix("rmat_batch64"))],
+    "batching": [("rmat_batch256", lambda: _batch_matrix("rmat_batch256"))],
 }
+# the batching workload: member count, largest member's rows, split K values
+# to partition for, partition cache
+BATCH = {"count": 256, "max_rows": 262144, "K": (16,), "cache": None}
 BATCHES = {}
+BATCH_LABELS = {}
+
+
+def _batch_member(spec):
+    """Worker (spawned process, no GPU): one member of the batch and its
+    row-column-net splits (Sec. 4.1) for each K."""
+    scale, deg, seed, Ks, cache = spec
+    import paper_1203_2739_gb300 as S
+    m, n, rp, ci, v = synth.rmat_batch_member(scale, deg, seed)
+    labels = {}
+    for K in Ks:
+        path = (os.path.join(cache, "batch_s%d_d%d_seed%d_rcn%d.npy" % (scale, deg, seed, K))
+                if cache else None)
+        if path and os.path.exists(path):
+            labels[K] = np.load(path)
+            continue
+        labels[K] = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_RCN, K=K, seed=0,
+                                     threads=1)["labels"]
+        if path:
+            os.makedirs(cache, exist_ok=True)
+            np.save(path, labels[K])
+    return (m, n, rp, ci, v), labels
 
 
 def _batch_matrix(name):
     """The batch as one block-diagonal CSR (the natural-form baseline runs it
-    as one matrix); the member matrices are kept for the batched plan."""
-    mats = synth.rmat_batch(64, seed=0)
-    BATCHES[name] = mats
+    as one matrix); the member matrices and their splits are kept for the
+    batched plan.  Members are generated and partitioned on spawned host
+    processes, largest first."""
+    import multiprocessing as mp
+    specs = synth.rmat_batch_specs(BATCH["count"], hi=BATCH["max_rows"], seed=0)
+    order = sorted(range(len(specs)), key=lambda b: -(specs[b][1] << specs[b][0]))
+    with mp.get_context("spawn").Pool(max(1, os.cpu_count() or 4)) as pool:
+        res = pool.map(_batch_member, [specs[b] + (tuple(BATCH["K"]), BATCH["cache"])
+                                       for b in order], chunksize=1)
+    mats, labels = [None] * len(specs), [None] * len(specs)
+    for b, (mat, lab) in zip(order, res):
+        mats[b], labels[b] = mat, lab
+    BATCHES[name], BATCH_LABELS[name] = mats, labels
     return synth.block_diagonal(mats)
 WORKLOAD_TEXT = {
     "sweep": "FP64 reordering sweep: mesh 1024^2 (5-pt, permuted), R-MAT 2^20 deg 16, "
              "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random, SB K=1024, "
              "DB K=1024, split K=4/16/64/256",
     "zipf16k": "Zipf 16384^2 (rows P(d)~d^-1.7498 on [1,512], Zipf(1.2) columns), natural vs SB",
-    "batching": "64 R-MAT matrices (rows log-uniform in [1024, 65536], power-of-two sizes, "
+    "batching": "256 R-MAT matrices (rows log-uniform in [1024, 262144], power-of-two sizes, "
                 "degree U[8,32]) in one plan: natural block-diagonal vs batched split K=16 "
                 "(row-column-net bisection of each matrix); FP32 with --dtype f32",
     "scale": "L2-exceeding point: 5-pt mesh 6144^2 (37.7M rows, 188.7M nnz, x = 302 MB), "
@@ -144,16 +185,21 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     return res
 
 
-def batched_split_plan(S, mats, K, dtype, threads):
+def batched_split_plan(S, name, K, dtype, threads, nrhs=1):
     """One plan over a batch of matrices, each split K ways by its own
     row-column-net bisection (Sec. 4.1)."""
-    def labels(mat):
-        m, n, rp, ci, _ = mat
-        return S.spmv_partition(m, n, rp, ci, S.SPMV_PART_RCN, K=K, seed=0,
-                                threads=1)["labels"]
-    with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
-        nz = list(ex.map(labels, mats))
-    return S.spmv_plan_create_batched(mats, nz_parts=nz, K=K, dtype=dtype)
+    mats = BATCHES[name]
+    known = BATCH_LABELS.get(name)
+    if known and all(K in lab for lab in known):
+        nz = [lab[K] for lab in known]
+    else:
+        def labels(mat):
+            m, n, rp, ci, _ = mat
+            return S.spmv_partition(m, n, rp, ci, S.SPMV_PART_RCN, K=K, seed=0,
+                                    threads=1)["labels"]
+        with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+            nz = list(ex.map(labels, mats))
+    return S.spmv_plan_create_batched(mats, nz_parts=nz, K=K, dtype=dtype, nrhs=nrhs)
 
 
 def form_kwargs(S, f, rp, ci, parts, seed=0):
@@ -378,6 +424,7 @@ def run_ours(args, rank, world, local_rank):
     dtype = {"f64": S.SPMV_F64, "f32": S.SPMV_F32, "bf16": S.SPMV_BF16}[args.dtype]
     vb, xb = {0: (8, 8), 1: (4, 4), 2: (2, 4)}[dtype]
     tdt = torch.float64 if dtype == S.SPMV_F64 else torch.float32
+    r = args.nrhs
     threads = max(1, (os.cpu_count() or 4) // 2)
     t_setup = time.perf_counter()
     mats = make_matrices(args.workload, log, args.matrices.split(",") if args.matrices else None)
@@ -399,8 +446,11 @@ def run_ours(args, rank, world, local_rank):
         for key, r in parts.items():
             log("  %s %s K=%d: partition %.1fs, cost %d (cols %d, rows %d)" % (
                 name, key[0], r["K"], r["seconds"], r["cost"], r["cost_cols"], r["cost_rows"]))
-        x = synth.uniform_x(n, 1)
-        y_ref, absax = oracle.spmv(m, n, rp, ci, v, x)
+        # X is n x r row-major; the oracle checks its first and last columns
+        x = synth.uniform_x(n, 1) if r == 1 else synth.uniform_x(n * r, 1).reshape(n, r)
+        cols = [0] if r == 1 else [0, r - 1]
+        refs = [oracle.spmv(m, n, rp, ci, v, x if r == 1 else np.ascontiguousarray(x[:, c]))
+                for c in cols]
         xt = torch.from_numpy(x).to(dev, dtype=tdt)
         for f in forms:
             kw, pres = form_kwargs(S, f, rp, ci, parts)
@@ -410,16 +460,16 @@ def run_ours(args, rank, world, local_rank):
             # 128 nonzeros reduced by a warp; or staging x), wide tiles, or
             # eight waves of smaller tiles (launched in order, so that the x windows of the
             # tiles running at once stay within L2 when x does not)
-            shapes = {"cta256": dict(dtype=dtype),
-                      "cta256w": dict(dtype=dtype, warp_rows=128),
-                      "cta256s": dict(dtype=dtype, flags=S.SPMV_FLAG_STAGE),
-                      "cta1024": dict(dtype=dtype, cta_threads=1024),
-                      "cta256x8": dict(dtype=dtype,
+            shapes = {"cta256": dict(dtype=dtype, nrhs=r),
+                      "cta256w": dict(dtype=dtype, nrhs=r, warp_rows=128),
+                      "cta256s": dict(dtype=dtype, nrhs=r, flags=S.SPMV_FLAG_STAGE),
+                      "cta1024": dict(dtype=dtype, nrhs=r, cta_threads=1024),
+                      "cta256x8": dict(dtype=dtype, nrhs=r,
                                        tile_nnz=max(1024, int(rp[-1]) // (8 * 912)))}
             if f.startswith("batch_split"):
-                plan = batched_split_plan(S, BATCHES[name], int(f[11:]), dtype, threads)
+                plan = batched_split_plan(S, name, int(f[11:]), dtype, threads, nrhs=r)
             elif f in ("natural", "random") or args.no_autotune:
-                plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, **kw)
+                plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, nrhs=r, **kw)
             elif args.shape:
                 plan = S.spmv_plan_create(m, n, rp, ci, v, **shapes[args.shape], **kw)
                 chosen = args.shape
@@ -430,22 +480,24 @@ def run_ours(args, rank, world, local_rank):
                 chosen = names[ibest]
             xh = torch.empty_like(xt)
             S.spmv_permute_x(plan, xt, xh)
-            yh = torch.empty(m, dtype=tdt, device=dev)
+            yh = torch.empty((m, r) if r > 1 else m, dtype=tdt, device=dev)
             S.spmv_exec(plan, xh, yh)
             y = torch.empty_like(yh)
             S.spmv_unpermute_y(plan, yh, y)
             torch.cuda.synchronize()
-            err = err_ratio(y.double().cpu().numpy(), y_ref, absax)
+            yc = y.double().cpu().numpy()
+            err = max(err_ratio(yc if r == 1 else yc[:, c], y_ref, absax)
+                      for c, (y_ref, absax) in zip(cols, refs))
             info = plan.info
             entries.append(dict(label="%s/%s" % (name, f), plan=plan, xh=xh, yh=yh,
-                                bytes=compulsory_bytes(m, n, int(rp[-1]), vb, xb),
-                                flops=2 * int(rp[-1]), err=err, info=info, tile_shape=chosen,
+                                bytes=compulsory_bytes(m, n, int(rp[-1]), vb, xb, r),
+                                flops=2 * int(rp[-1]) * r, err=err, info=info, tile_shape=chosen,
                                 cost=None if pres is None else int(pres["cost"]),
                                 part_s=None if pres is None else float(pres["seconds"])))
             log("  plan %s/%s: K=%d tiles=%d staged=%d shape=%s err=%.2e (%.1fs)" % (
                 name, f, info["K"], info["n_tiles"], info["n_staged_tiles"], chosen, err,
                 time.perf_counter() - t1))
-        del y_ref, absax
+        del refs
     setup_s = time.perf_counter() - t_setup
 
     def step(events=None):
@@ -567,6 +619,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD_TEXT[args.workload],
                    "matrices": [m[0] for m in mats], "forms": forms,
                    "unit_of_work": "one y<-Ax per (matrix, form) per step",
+                   "nrhs": r,
                    "l2": "inputs larger than L2: each step streams %.2f GB over %d plans"
                          % (step_bytes / 1e9, len(entries)),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -823,7 +876,24 @@ def main():
                     help="tiled forms with this tile shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")
+    ap.add_argument("--nrhs", type=int, default=1, choices=[1, 2, 4, 8],
+                    help="right-hand sides per product (Y = A X, X row-major n x nrhs)")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="matrices in the batching workload")
+    ap.add_argument("--batch-max-rows", type=int, default=262144,
+                    help="largest member of the batching workload (rows, log-uniform from 1024)")
     args = ap.parse_args()
+    if args.workload == "batching":
+        name = "rmat_batch%d" % args.batch_count
+        BATCH.update(count=args.batch_count, max_rows=args.batch_max_rows,
+                     cache=args.partition_cache,
+                     K=() if args.impl == "reference" else tuple(
+                         int(f[11:]) for f in (args.forms or "batch_split16").split(",")
+                         if f.startswith("batch_split")))
+        MATRICES["batching"] = [(name, lambda: _batch_matrix(name))]
+        WORKLOAD_TEXT["batching"] = WORKLOAD_TEXT["batching"].replace(
+            "256 R-MAT", "%d R-MAT" % args.batch_count).replace(
+            "262144]", "%d]" % args.batch_max_rows)
     if args.scale_nx != 6144:
         nx = args.scale_nx
         MATRICES["scale"] = [("mesh5_%d" % nx, lambda: synth.mesh5(nx, seed=0))]

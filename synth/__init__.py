@@ -263,19 +263,31 @@ def laplacian3d(n=128, seed=0, permute=True):
     return coo_to_csr(N, N, rows, cols, vals)
 
 
-def rmat_batch(count=64, lo=1024, hi=65536, deg_lo=8, deg_hi=32, seed=0):
-    """`count` R-MAT matrices (a, b, c = .57, .19, .19) with row counts drawn
-    log-uniformly in [lo, hi] and rounded to a power of two (R-MAT's own
-    sizes), average degree uniform in [deg_lo, deg_hi], seeds seed..seed+count-1.
-    Returns a list of (m, n, rowptr, colidx, vals)."""
+def rmat_batch_specs(count=64, lo=1024, hi=65536, deg_lo=8, deg_hi=32, seed=0):
+    """The members of rmat_batch as (scale, degree, seed) triples: row counts
+    drawn log-uniformly in [lo, hi] and rounded to a power of two (R-MAT's
+    own sizes), average degree uniform in [deg_lo, deg_hi], seeds
+    seed..seed+count-1."""
     rng = _rng(seed)
     out = []
     for b in range(count):
         scale = int(round(rng.uniform(np.log2(lo), np.log2(hi))))
         deg = int(rng.integers(deg_lo, deg_hi + 1))
-        rp, ci, v = rmat(scale, deg, seed=seed + b, chunk=1 << 18)
-        out.append((1 << scale, 1 << scale, rp, ci, v))
+        out.append((scale, deg, seed + b))
     return out
+
+
+def rmat_batch_member(scale, deg, seed):
+    """One member of rmat_batch: (m, n, rowptr, colidx, vals)."""
+    rp, ci, v = rmat(scale, deg, seed=seed, chunk=1 << 18)
+    return (1 << scale, 1 << scale, rp, ci, v)
+
+
+def rmat_batch(count=64, lo=1024, hi=65536, deg_lo=8, deg_hi=32, seed=0):
+    """`count` R-MAT matrices (a, b, c = .57, .19, .19) with the sizes and
+    degrees of rmat_batch_specs.  Returns a list of (m, n, rowptr, colidx,
+    vals)."""
+    return [rmat_batch_member(*s) for s in rmat_batch_specs(count, lo, hi, deg_lo, deg_hi, seed)]
 
 
 def block_diagonal(mats):

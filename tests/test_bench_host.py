@@ -55,3 +55,33 @@ def test_split_forms_are_cuts_of_one_tree():
         assert kw["row_part_ptr"].size == K + 2 and kw["col_part_ptr"].size == K + 2
         assert kw["row_part_ptr"][-1] == m and kw["col_part_ptr"][-1] == n
         assert np.all(np.diff(kw["col_part_ptr"]) >= 0)
+
+
+def test_batch_members_match_the_serial_generator_and_are_split(tmp_path):
+    """The batching workload's members, generated and partitioned on spawned
+    processes, are the matrices of synth.rmat_batch, each with a valid
+    K = 16 row-column-net split; the partition cache returns the same
+    labels."""
+    saved = dict(bench.BATCH)
+    try:
+        bench.BATCH.update(count=6, max_rows=8192, K=(16,), cache=str(tmp_path))
+        rp, ci, v = bench._batch_matrix("t")
+        ref = synth.rmat_batch(6, lo=1024, hi=8192, seed=0)
+        got = bench.BATCHES["t"]
+        assert [g[0] for g in got] == [r[0] for r in ref]
+        for g, r in zip(got, ref):
+            for a, b in zip(g[2:], r[2:]):
+                assert np.array_equal(a, b)
+        brp, bci, bv = synth.block_diagonal(ref)
+        assert np.array_equal(rp, brp) and np.array_equal(ci, bci) and np.array_equal(v, bv)
+        labs = bench.BATCH_LABELS["t"]
+        for (m, n, mrp, mci, _), lab in zip(got, labs):
+            assert lab[16].shape == (int(mrp[-1]),)
+            assert lab[16].min() >= 0 and lab[16].max() < 16
+        assert len(os.listdir(tmp_path)) == 6
+        bench._batch_matrix("t2")
+        for a, b in zip(labs, bench.BATCH_LABELS["t2"]):
+            assert np.array_equal(a[16], b[16])
+    finally:
+        bench.BATCH.clear()
+        bench.BATCH.update(saved)
