@@ -443,9 +443,10 @@ def run_ours(args, rank, world, local_rank):
     for (name, rp, ci, v), parts in zip(mats, all_parts):
         m = n = len(rp) - 1
         parts_kept = parts
-        for key, r in parts.items():
+        for key, pr in parts.items():
             log("  %s %s K=%d: partition %.1fs, cost %d (cols %d, rows %d)" % (
-                name, key[0], r["K"], r["seconds"], r["cost"], r["cost_cols"], r["cost_rows"]))
+                name, key[0], pr["K"], pr["seconds"], pr["cost"], pr["cost_cols"],
+                pr["cost_rows"]))
         # X is n x r row-major; the oracle checks its first and last columns
         x = synth.uniform_x(n, 1) if r == 1 else synth.uniform_x(n * r, 1).reshape(n, r)
         cols = [0] if r == 1 else [0, r - 1]

@@ -35,6 +35,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 
 #include "spmv_device.h"
@@ -200,6 +201,38 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
     return false;
 }
 
+// The R entries of one column index in a row-major n x R block of vectors
+// (global memory when GLOBAL, else shared memory): 16-byte loads where the
+// R entries fill whole 16-byte words, one 8-byte load for two FP32 entries,
+// scalar loads otherwise (R = 1).  x_hat and the staged window start on 16
+// bytes and a column's block is R entries long, so every such load is
+// aligned.
+template <int R, typename XT, bool GLOBAL>
+__device__ __forceinline__ void load_xrow(const XT *p, XT (&o)[R])
+{
+    constexpr int B = R * (int)sizeof(XT);
+    if constexpr (B >= 16 && B % 16 == 0) {
+        using V = typename std::conditional<sizeof(XT) == 8, double2, float4>::type;
+        constexpr int per = 16 / (int)sizeof(XT);
+#pragma unroll
+        for (int c = 0; c < R; c += per) {
+            const V *q = reinterpret_cast<const V *>(p + c);
+            const V t = GLOBAL ? __ldg(q) : *q;
+            const XT *e = reinterpret_cast<const XT *>(&t);
+#pragma unroll
+            for (int k = 0; k < per; ++k) o[c + k] = e[k];
+        }
+    } else if constexpr (B == 8 && sizeof(XT) == 4) {
+        const float2 *q = reinterpret_cast<const float2 *>(p);
+        const float2 t = GLOBAL ? __ldg(q) : *q;
+        o[0] = t.x;
+        o[1] = t.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < R; ++c) o[c] = GLOBAL ? __ldg(p + c) : p[c];
+    }
+}
+
 // ------------------------------------------------ plain CSR, vector per row --
 template <int LANES, int R, typename VT, typename XT>
 __global__ void __launch_bounds__(kThreads)
@@ -217,8 +250,10 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
         for (int32_t p = p0 + (int32_t)threadIdx.x; p < p1; p += kThreads) {
             const XT v = (XT)load_val(val + p);
             const int64_t xc = (int64_t)ld_stream(col + p) * R;
+            XT xo[R];
+            load_xrow<R, XT, true>(x + xc, xo);
 #pragma unroll
-            for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
+            for (int c = 0; c < R; ++c) s[c] = fma(v, xo[c], s[c]);
         }
         block_sum<R>(s);
         if (threadIdx.x == 0) {
@@ -245,8 +280,10 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
     for (int32_t p = p0 + lane; p < p1; p += LANES) {
         const XT v = (XT)load_val(val + p);
         const int64_t xc = (int64_t)ld_stream(col + p) * R;
+        XT xo[R];
+        load_xrow<R, XT, true>(x + xc, xo);
 #pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
+        for (int c = 0; c < R; ++c) s[c] = fma(v, xo[c], s[c]);
     }
 #pragma unroll
     for (int c = 0; c < R; ++c) s[c] = group_sum<LANES>(s[c]);
@@ -289,21 +326,18 @@ __device__ __forceinline__ void fetch_x(int32_t ci, const XT *seg, const XT *__r
                                         XT (&o)[R])
 {
     if (KIND == TILE_NARROW) {
-#pragma unroll
-        for (int c = 0; c < R; ++c) o[c] = seg[ci * R + c];
+        load_xrow<R, XT, false>(seg + ci * R, o);
     } else if (KIND == TILE_GLOBAL) {
-#pragma unroll
-        for (int c = 0; c < R; ++c) o[c] = __ldg(x + (int64_t)ci * R + c);
+        load_xrow<R, XT, true>(x + (int64_t)ci * R, o);
     } else {
         const bool g = ci < 0;
         const int64_t gi = g ? (int64_t)(~ci) : 0;
         const int32_t si = g ? 0 : ci;
+        XT a[R], b[R];
+        load_xrow<R, XT, true>(x + gi * R, a);
+        load_xrow<R, XT, false>(seg + si * R, b);
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            const XT a = __ldg(x + gi * R + c);
-            const XT b = seg[si * R + c];
-            o[c] = g ? a : b;
-        }
+        for (int c = 0; c < R; ++c) o[c] = g ? a[c] : b[c];
     }
 }
 
@@ -456,8 +490,10 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
         for (int32_t e = t.e0 + (int32_t)threadIdx.x; e < t.e1; e += NT) {
             const XT v = (XT)load_val(val + e);
             const int64_t xc = (int64_t)ld_stream(c32 + e) * R;
+            XT xo[R];
+            load_xrow<R, XT, true>(x + xc, xo);
 #pragma unroll
-            for (int c = 0; c < R; ++c) s[c] = fma(v, __ldg(x + xc + c), s[c]);
+            for (int c = 0; c < R; ++c) s[c] = fma(v, xo[c], s[c]);
         }
         block_sum<R, XT, NT>(s);
         if (threadIdx.x == 0) {
