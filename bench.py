@@ -237,6 +237,19 @@ def form_kwargs(S, f, rp, ci, parts, seed=0):
     raise ValueError(f)
 
 
+def tile_shapes(S, dtype, nrhs, nnz):
+    """The launch shapes the autotuner chooses from for a tiled plan: one
+    wave of 256-thread tiles (rows over 64, or over 128, nonzeros reduced by
+    a warp; or staging x), wide 1024-thread tiles, or eight waves of smaller
+    tiles (launched in order, so that the x windows of the tiles running at
+    once stay within L2 when x does not)."""
+    return {"cta256": dict(dtype=dtype, nrhs=nrhs),
+            "cta256w": dict(dtype=dtype, nrhs=nrhs, warp_rows=128),
+            "cta256s": dict(dtype=dtype, nrhs=nrhs, flags=S.SPMV_FLAG_STAGE),
+            "cta1024": dict(dtype=dtype, nrhs=nrhs, cta_threads=1024),
+            "cta256x8": dict(dtype=dtype, nrhs=nrhs, tile_nnz=max(1024, nnz // (8 * 912)))}
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -457,16 +470,7 @@ def run_ours(args, rank, world, local_rank):
             kw, pres = form_kwargs(S, f, rp, ci, parts)
             t1 = time.perf_counter()
             chosen = None
-            # tile shapes: one wave of 256-thread tiles (rows over 64 or over
-            # 128 nonzeros reduced by a warp; or staging x), wide tiles, or
-            # eight waves of smaller tiles (launched in order, so that the x windows of the
-            # tiles running at once stay within L2 when x does not)
-            shapes = {"cta256": dict(dtype=dtype, nrhs=r),
-                      "cta256w": dict(dtype=dtype, nrhs=r, warp_rows=128),
-                      "cta256s": dict(dtype=dtype, nrhs=r, flags=S.SPMV_FLAG_STAGE),
-                      "cta1024": dict(dtype=dtype, nrhs=r, cta_threads=1024),
-                      "cta256x8": dict(dtype=dtype, nrhs=r,
-                                       tile_nnz=max(1024, int(rp[-1]) // (8 * 912)))}
+            shapes = tile_shapes(S, dtype, r, int(rp[-1]))
             if f.startswith("batch_split"):
                 plan = batched_split_plan(S, name, int(f[11:]), dtype, threads, nrhs=r)
             elif f in ("natural", "random") or args.no_autotune:
