@@ -72,15 +72,57 @@ struct HG {
 
     i64 pins_of(i32 n) const { return xpins[n + 1] - xpins[n]; }
 
-    void build_vertex_side()
+    // The transpose: the nets of each vertex in increasing order.  With
+    // several threads each takes a range of nets, counts its pins per
+    // vertex and writes after the threads before it, so the result is the
+    // serial one (used on coarse levels: few vertices, many pins).
+    void build_vertex_side(int threads = 1)
     {
+        const i64 np = (i64)pins.size();
         xnets.assign((size_t)nv + 1, 0);
-        for (i64 q = 0; q < (i64)pins.size(); ++q) xnets[pins[q] + 1]++;
-        for (i32 v = 0; v < nv; ++v) xnets[v + 1] += xnets[v];
-        nets.resize(pins.size());
-        std::vector<i64> pos(xnets.begin(), xnets.end() - 1);
-        for (i32 n = 0; n < nn; ++n)
-            for (i64 q = xpins[n]; q < xpins[n + 1]; ++q) nets[pos[pins[q]]++] = n;
+        nets.resize((size_t)np);
+        int T = std::max(1, threads);
+        if (np < (1 << 20)) T = 1;
+        T = (int)std::min<i64>(T, std::max<i64>(1, ((i64)64 << 20) / (8 * std::max<i32>(nv, 1))));
+        if (T == 1) {
+            for (i64 q = 0; q < np; ++q) xnets[pins[q] + 1]++;
+            for (i32 v = 0; v < nv; ++v) xnets[v + 1] += xnets[v];
+            std::vector<i64> pos(xnets.begin(), xnets.end() - 1);
+            for (i32 n = 0; n < nn; ++n)
+                for (i64 q = xpins[n]; q < xpins[n + 1]; ++q) nets[pos[pins[q]]++] = n;
+            return;
+        }
+        // net ranges of about np / T pins each
+        std::vector<i32> nb((size_t)T + 1, nn);
+        nb[0] = 0;
+        for (int t = 1; t < T; ++t)
+            nb[t] = (i32)(std::lower_bound(xpins.begin(), xpins.begin() + nn, np * t / T) -
+                          xpins.begin());
+        std::vector<std::vector<i64>> off((size_t)T, std::vector<i64>((size_t)nv, 0));
+        auto run = [&](auto &&body) {
+            std::vector<std::thread> ts;
+            for (int t = 1; t < T; ++t) ts.emplace_back(body, t);
+            body(0);
+            for (auto &th : ts) th.join();
+        };
+        run([&](int t) {
+            std::vector<i64> &c = off[t];
+            for (i64 q = xpins[nb[t]]; q < xpins[nb[t + 1]]; ++q) c[pins[q]]++;
+        });
+        for (i32 v = 0; v < nv; ++v) {
+            i64 at = xnets[v];
+            for (int t = 0; t < T; ++t) {
+                const i64 c = off[t][v];
+                off[t][v] = at;
+                at += c;
+            }
+            xnets[v + 1] = at;
+        }
+        run([&](int t) {
+            std::vector<i64> &o = off[t];
+            for (i32 n = nb[t]; n < nb[t + 1]; ++n)
+                for (i64 q = xpins[n]; q < xpins[n + 1]; ++q) nets[o[pins[q]]++] = n;
+        });
     }
 };
 
@@ -276,7 +318,7 @@ struct Coarsen {
             P = Part();
         }
         merge_identical(C);
-        C.build_vertex_side();
+        C.build_vertex_side(threads);
         return C;
     }
 
@@ -436,6 +478,8 @@ struct FM {
     void init_counts()
     {
         cnt.assign((size_t)G.nn * 2, 0);
+        tracked = true;
+        for (i32 n = 0; n < G.nn && tracked; ++n) tracked = G.pins_of(n) <= kBigNet;
         w[0] = w[1] = 0;
         for (i32 v = 0; v < G.nv; ++v) w[side[v]] += G.vw[v];
         for (i32 n = 0; n < G.nn; ++n)
@@ -464,6 +508,12 @@ struct FM {
 
     std::vector<i32> pending;        // vertices entering the candidate set
     std::vector<uint8_t> is_pending;
+    // gain_ok[u]: gain[u] is exact although u is not in a heap (it left one
+    // as infeasible, or entered the candidate set earlier in the pass), so
+    // re-entering costs no recount of its nets.  Kept only when every net
+    // gets the per-move updates (none above kBigNet pins).
+    std::vector<uint8_t> gain_ok;
+    bool tracked = true;
     // gain changes of one move, summed per vertex before the heaps see them
     // (at coarse levels a move touches the same few vertices through
     // thousands of nets)
@@ -493,11 +543,14 @@ struct FM {
                     gain[u] += d;
                     heap[side[u]].update(u);
                 }
-            } else if (!is_pending[u]) {
-                // not a candidate yet: its exact gain is computed once the
-                // move is complete
-                is_pending[u] = 1;
-                pending.push_back(u);
+            } else {
+                if (gain_ok[u]) gain[u] += d;
+                if (!is_pending[u]) {
+                    // not in a heap: it re-enters once the move is complete
+                    // (with its gain counted then if it was never known)
+                    is_pending[u] = 1;
+                    pending.push_back(u);
+                }
             }
         }
         touched.clear();
@@ -508,7 +561,10 @@ struct FM {
         for (i32 u : pending) {
             is_pending[u] = 0;
             if (locked[u] || pos[u] >= 0) continue;
-            gain[u] = vgain(u);
+            if (!gain_ok[u]) {
+                gain[u] = vgain(u);
+                gain_ok[u] = tracked;
+            }
             heap[side[u]].push(u);
         }
         pending.clear();
@@ -528,6 +584,7 @@ struct FM {
         i64 total = 0;
         for (int pass = 0; pass < passes; ++pass) {
             locked.assign((size_t)G.nv, 0);
+            gain_ok.assign((size_t)G.nv, 0);
             for (i32 v = 0; v < G.nv; ++v) tb[v] = (uint32_t)rng();
             heap[0].h.clear();
             heap[1].h.clear();
@@ -541,6 +598,7 @@ struct FM {
                     }
                 if (!cand) continue;
                 gain[v] = vgain(v);
+                gain_ok[v] = tracked;
                 heap[side[v]].push(v);
             }
             std::vector<i32> moves;
@@ -684,9 +742,11 @@ void grow(const HG &G, i64 target0, std::mt19937_64 &rng, std::vector<uint8_t> &
     fm.delta.assign((size_t)G.nv, 0);
     fm.is_touched.assign((size_t)G.nv, 0);
     fm.locked.assign((size_t)G.nv, 0);
+    fm.gain_ok.assign((size_t)G.nv, 0);
     for (i32 v = 0; v < G.nv; ++v) {
         fm.tb[v] = (uint32_t)rng();
         fm.gain[v] = fm.vgain(v);
+        fm.gain_ok[v] = fm.tracked;
         fm.heap[1].push(v);
     }
     i32 v = (i32)(rng() % (u64)G.nv);       // random seed vertex first

@@ -237,3 +237,16 @@ def test_bisection_against_enumeration_on_tiny_hypergraphs(case):
     excess = got[:, 0] - got[:, 1]
     assert excess.min() >= 0
     assert (excess == 0).mean() >= 0.97 and excess.max() <= 1, excess
+
+
+def test_parallel_coarsening_matches_serial_on_a_large_hypergraph():
+    """Above a million pins the coarse levels' vertex-to-net lists are built
+    by several threads; the partition must be the serial one."""
+    rp, ci, _ = synth.rmat(16, 20, seed=4)
+    m = n = 1 << 16
+    assert rp[-1] > (1 << 20)
+    for method in (S.SPMV_PART_CN, S.SPMV_PART_RCN):
+        a = S.spmv_partition(m, n, rp, ci, method, K=4, seed=2, threads=1)
+        b = S.spmv_partition(m, n, rp, ci, method, K=4, seed=2, threads=6)
+        assert np.array_equal(a["labels"], b["labels"]) and a["cost"] == b["cost"]
+        assert a["cost"] == _bound(a, m, n, rp, ci)
