@@ -202,7 +202,8 @@ spmv_status spmv_plan_create_batched(int32_t count, const spmv_csr *A, const spm
  * k = 1..K (Sec. 4), on `stream`.  x_hat: n*r device elements, y_hat: m*r
  * device elements (double for F64, float for F32/BF16), row major, no
  * aliasing; x_hat 16-byte aligned (SPMV_E_INVALID otherwise: tiles copy
- * their x segments with bulk copies that need it).  y_hat is overwritten.
+ * their x segments with bulk copies that need it, and with r > 1 the r
+ * entries of a column are read as 16-byte words).  y_hat is overwritten.
  * Asynchronous. */
 spmv_status spmv_exec(spmv_plan *plan, const void *x_hat, void *y_hat, void *stream);
 
