@@ -317,22 +317,34 @@ struct Coarsen {
             C.nid.insert(C.nid.end(), P.nid.begin(), P.nid.end());
             P = Part();
         }
-        merge_identical(C);
+        merge_identical(C, threads);
         C.build_vertex_side(threads);
         return C;
     }
 
     // Nets with the same pin set are cut together: keep one with the summed
     // cost (coarse levels only; the split bookkeeping uses the finest level).
-    static void merge_identical(HG &C)
+    static void merge_identical(HG &C, int threads = 1)
     {
         if (C.nn < 2) return;
         std::vector<std::pair<u64, i32>> key((size_t)C.nn);
-        for (i32 n = 0; n < C.nn; ++n) {
-            u64 h = 1469598103934665603ULL ^ (u64)C.pins_of(n);
-            for (i64 q = C.xpins[n]; q < C.xpins[n + 1]; ++q)
-                h = (h ^ (u64)C.pins[q]) * 1099511628211ULL;
-            key[n] = {h, n};
+        auto hash = [&](int t, int T) {
+            const i32 b = (i32)((i64)C.nn * t / T), e = (i32)((i64)C.nn * (t + 1) / T);
+            for (i32 n = b; n < e; ++n) {
+                u64 h = 1469598103934665603ULL ^ (u64)C.pins_of(n);
+                for (i64 q = C.xpins[n]; q < C.xpins[n + 1]; ++q)
+                    h = (h ^ (u64)C.pins[q]) * 1099511628211ULL;
+                key[n] = {h, n};
+            }
+        };
+        const int T = C.pins.size() > (1u << 20) ? std::max(1, threads) : 1;
+        if (T == 1) {
+            hash(0, 1);
+        } else {
+            std::vector<std::thread> ts;
+            for (int t = 1; t < T; ++t) ts.emplace_back(hash, t, T);
+            hash(0, T);
+            for (auto &th : ts) th.join();
         }
         std::sort(key.begin(), key.end());
         std::vector<i32> keep_of((size_t)C.nn, -1);
