@@ -96,3 +96,45 @@ def test_tile_shapes_are_the_autotuner_candidates():
     # eight waves of 152 SMs x 6 resident CTAs
     assert sh["cta256x8"]["tile_nnz"] == 36_000_000 // (8 * 912)
     assert bench.tile_shapes(S, 0, 1, 1000)["cta256x8"]["tile_nnz"] == 1024
+
+
+class _FakeSmi:
+    """Stands in for the nvidia-smi sampling process: canned CSV rows in
+    the order of ClockSampler.FIELDS."""
+
+    def __init__(self, text):
+        self.text = text
+        self.terminated = False
+
+    def terminate(self):
+        self.terminated = True
+
+    def communicate(self, timeout=None):
+        return self.text, ""
+
+
+def test_clock_sampler_reports_median_max_and_throttle_reasons():
+    rows = [
+        "1980, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2070, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1250.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "[N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    cs = bench.ClockSampler(0)
+    cs.proc = _FakeSmi("\n".join(rows) + "\n")
+    out = cs.stop()
+    assert cs.proc.terminated
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+    cs.proc = _FakeSmi("2070, 2070, 1.0, 0x8, Active, Not Active, Active, Not Active\n")
+    assert cs.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    cs.proc = _FakeSmi("")
+    assert cs.stop() is None
+    assert bench.ClockSampler(0).stop() is None      # never started
+
+
+def test_whole_job_throughput_counts_every_rank():
+    # 2 ranks, 1 GB each per 1 ms step: 2000 GB/s for the job
+    assert bench.whole_job_gbs(2, 1e9, 1.0) == pytest.approx(2000.0)
+    assert bench.whole_job_gbs(1, 5e8, 0.5) == pytest.approx(1000.0)
