@@ -138,3 +138,44 @@ def test_whole_job_throughput_counts_every_rank():
     # 2 ranks, 1 GB each per 1 ms step: 2000 GB/s for the job
     assert bench.whole_job_gbs(2, 1e9, 1.0) == pytest.approx(2000.0)
     assert bench.whole_job_gbs(1, 5e8, 0.5) == pytest.approx(1000.0)
+
+
+def _copy_sources(tmp_path):
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_1203_2739_gb300", "csrc")
+    dst = tmp_path / "paper_1203_2739_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), dst / f)
+    return dst
+
+
+def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The DRAM traffic of an ncu capture is used only while the kernel and
+    plan sources are those it was taken from; edits to comments alone keep
+    it."""
+    import json
+    dst = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel_source_hash": h0,
+           "entries": {"m/f k<1>": {"dram_bytes_per_launch": 123}}}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
+    assert bench.ncu_traffic("m/f", "k<1>") == 123
+    assert bench.ncu_traffic("m/g", "k<1>") is None
+    k = dst / "spmv_kernels.cuh"
+    k.write_text(k.read_text() + "\n// a comment only\n/* and a block\n comment */\n")
+    assert bench.kernel_source_hash() == h0
+    assert bench.ncu_traffic("m/f", "k<1>") == 123
+    k.write_text(k.read_text() + "\nstatic int changed_code = 1;\n")
+    assert bench.kernel_source_hash() != h0
+    assert bench.ncu_traffic("m/f", "k<1>") is None
+
+
+def test_measured_peak_and_fallback(tmp_path, monkeypatch):
+    import json
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peak() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6697.2}))
+    assert bench.measured_peak() == (6697.2, "measured")
