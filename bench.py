@@ -387,7 +387,11 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": round(1e3 * t / max(args.steps, 1), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload]},
+        "config": {"workload": WORKLOAD_TEXT[args.workload],
+                   "matrices": [p[0] for p in prepared],
+                   "unit_of_work": "one y<-Ax of one whole matrix per step, the matrices in turn "
+                                   "(every form of the method computes this same product)",
+                   "nrhs": 1, "parallelism": "1 host thread"},
         "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,

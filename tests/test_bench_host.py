@@ -179,3 +179,30 @@ def test_measured_peak_and_fallback(tmp_path, monkeypatch):
     assert bench.measured_peak() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6697.2}))
     assert bench.measured_peak() == (6697.2, "measured")
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference times the CPU oracle (no GPU needed) and
+    prints the contract's JSON line."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
+                          "reference", "--workload", "zipf16k", "--steps", "3", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 3 and d["warmup"] == 1
+    assert d["metric"].startswith("SpMV GB/s") and d["unit"] == "GB/s"
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["config"]["workload"] == bench.WORKLOAD_TEXT["zipf16k"]
+    assert d["config"]["matrices"] == ["zipf16k"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    sel = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
+                          "reference", "--workload", "selector"],
+                         capture_output=True, text=True, timeout=300, check=True).stdout
+    assert "unavailable" in json.loads(sel.strip().splitlines()[-1])
