@@ -91,7 +91,9 @@ def _batch_matrix(name):
     import multiprocessing as mp
     specs = synth.rmat_batch_specs(BATCH["count"], hi=BATCH["max_rows"], seed=0)
     order = sorted(range(len(specs)), key=lambda b: -(specs[b][1] << specs[b][0]))
-    with mp.get_context("spawn").Pool(max(1, os.cpu_count() or 4)) as pool:
+    # at most 32 workers: each holds one member and its hypergraph (up to a
+    # few GB for the largest)
+    with mp.get_context("spawn").Pool(max(1, min(32, os.cpu_count() or 4))) as pool:
         res = pool.map(_batch_member, [specs[b] + (tuple(BATCH["K"]), BATCH["cache"])
                                        for b in order], chunksize=1)
     mats, labels = [None] * len(specs), [None] * len(specs)
