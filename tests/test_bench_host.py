@@ -206,3 +206,45 @@ def test_reference_arm_prints_one_contract_line():
                           "reference", "--workload", "selector"],
                          capture_output=True, text=True, timeout=300, check=True).stdout
     assert "unavailable" in json.loads(sel.strip().splitlines()[-1])
+
+
+class _HostS:
+    """A stand-in for the library on host tensors (natural form only), to
+    run bench.library_reference without a GPU."""
+    SPMV_F64 = 0
+
+    def __init__(self):
+        self.live = 0
+
+    def spmv_plan_create(self, m, n, rp, ci, vals, dtype=0, nrhs=1):
+        import scipy.sparse as sp
+        self.live += 1
+        return (sp.csr_matrix((np.asarray(vals, dtype=np.float64), ci, rp), shape=(m, n)), nrhs)
+
+    def spmv_exec(self, plan, x, y):
+        import torch
+        A, r = plan
+        assert x.is_contiguous() and x.numel() == A.shape[1] * r
+        y.copy_(torch.from_numpy(np.asarray(A @ x.numpy()).reshape(y.shape)))
+
+    def spmv_plan_destroy(self, plan):
+        self.live -= 1
+
+
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_library_reference_is_y_and_abs_product(nrhs):
+    import torch
+    import oracle
+    m, n = 300, 280
+    rp, ci, v = synth.random_sparse(m, n, 0.05, 3, integer=False)
+    x = synth.uniform_x(n * nrhs, 2).reshape(n, nrhs) if nrhs > 1 else synth.uniform_x(n, 2)
+    fake = _HostS()
+    y, absax = bench.library_reference(fake, m, n, rp, ci, v, torch.from_numpy(x))
+    assert fake.live == 0
+    for c in range(nrhs):
+        xc = x if nrhs == 1 else np.ascontiguousarray(x[:, c])
+        want, want_abs = oracle.spmv(m, n, rp, ci, v, xc)
+        got = y if nrhs == 1 else y[:, c]
+        got_abs = absax if nrhs == 1 else absax[:, c]
+        assert np.allclose(got, want, rtol=1e-13, atol=1e-13)
+        assert np.allclose(got_abs, want_abs, rtol=1e-13, atol=1e-13)
