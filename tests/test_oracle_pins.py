@@ -284,6 +284,40 @@ def test_lru_golden_traces():
         assert out[0] == t["misses"], t
 
 
+def _textbook_lru(arrays, indices, lines, line_bytes):
+    """Fully associative LRU over (array, line) keys with an ordered dict:
+    a hit moves the line to the back, a miss evicts the front when full."""
+    from collections import OrderedDict
+    cache, misses = OrderedDict(), np.zeros(6, dtype=np.int64)
+    for a, i in zip(arrays, indices):
+        key = (int(a), int(i) * 8 // line_bytes)
+        if key in cache:
+            cache.move_to_end(key)
+            continue
+        misses[a] += 1
+        cache[key] = True
+        if len(cache) > lines:
+            cache.popitem(last=False)
+    return misses
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lru_matches_a_textbook_lru_on_random_traces(seed):
+    """The simulator's hashed, linked-list LRU against an ordered-dict LRU
+    on random traces of several arrays, for several capacities and lines."""
+    rng = np.random.default_rng(seed)
+    n = 3000
+    arrays = rng.integers(0, 6, n).astype(np.int32)
+    # a skewed index mix: some reuse at every distance
+    indices = np.where(rng.random(n) < 0.5, rng.integers(0, 40, n),
+                       rng.integers(0, 2000, n)).astype(np.int64)
+    for line_bytes in (8, 64):
+        for lines in (1, 2, 7, 64, 500):
+            got = oracle.cachesim_trace(arrays, indices, lines * line_bytes, line_bytes)
+            want = _textbook_lru(arrays, indices, lines, line_bytes)
+            assert np.array_equal(got, want), (line_bytes, lines)
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_lru_compulsory_misses_when_everything_fits(seed):
     rp, ci, v = synth.random_sparse(50, 60, 0.1, seed)
