@@ -50,6 +50,27 @@ def test_spmv_equals_dense_matvec_exactly(seed, shape):
     assert np.array_equal(Y, A @ X)
 
 
+def test_spmv_sums_are_compensated():
+    """The oracle's row sums carry a running error term (Neumaier), so
+    cancellation that a plain left-to-right FP64 sum gets wrong comes out
+    exact: 1e16 + 1 - 1e16 = 1 (plain: 0), and the sum of 10^5 copies of 0.1
+    after 1e8 matches the exactly rounded value."""
+    rp = np.array([0, 3, 6], dtype=np.int64)
+    ci = np.array([0, 1, 2, 0, 1, 2], dtype=np.int32)
+    v = np.array([1e16, 1.0, -1e16, 1.0, 1e16, -1e16])
+    y, a = oracle.spmv(2, 3, rp, ci, v, np.ones(3))
+    assert y[0] == 1.0 and y[1] == 1.0
+    assert a[0] == 2e16 + 1.0
+    k = 100_000
+    rp = np.array([0, k + 1], dtype=np.int64)
+    ci = np.arange(k + 1, dtype=np.int32)
+    v = np.r_[1e8, np.full(k, 0.1)]
+    y, _ = oracle.spmv(1, k + 1, rp, ci, v, np.ones(k + 1))
+    from fractions import Fraction
+    exact = Fraction(1e8) + k * Fraction(0.1)
+    assert y[0] == float(exact)
+
+
 def test_spmv_laplacian_eigenvector_closed_form():
     """Dirichlet 3D Laplacian: v = sin(i pi a/(N+1)) sin(j pi b/(N+1))
     sin(k pi c/(N+1)) is an eigenvector with eigenvalue
