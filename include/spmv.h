@@ -430,6 +430,26 @@ spmv_status spmv_csr_exec_noalloc(int32_t m, int32_t n, int64_t nnz,
                                   const double *vals_dev, const double *x_dev,
                                   double *y_dev, void *stream);
 
+/* Diagnostics: build the host image of the plan spmv_plan_create would build
+ * for A, perm, splits and opts on a device with n_sm SMs (0 = 152, GB300),
+ * and evaluate the product by walking that image the way the kernels do
+ * (Sec. 3: y_hat = A_hat x_hat; Sec. 4: the sum over k of A^k x_hat, through
+ * the partial slots and the fix-ups), on the host in FP64.  No device call.
+ * x (n x r) and y (m x r, overwritten) are host arrays in the ORIGINAL
+ * order, row major, r = opts->nrhs; values are used in FP64 whatever
+ * opts->dtype says (the image's layout is the one of that dtype).  Every
+ * index of the image is checked against its array, and every row of y and
+ * every partial slot must be written exactly once: a violation returns
+ * SPMV_E_INTERNAL with the offending indices in spmv_last_error().
+ * stats (may be NULL) receives SPMV_EMULATE_STATS counts: tiles, chunk
+ * tiles, staged tiles, partial slots, fix-ups, warp rows, stored chunk
+ * elements (with padding), 1 if the plain CSR kernel is used.  Errors: those
+ * of spmv_plan_create's validation, SPMV_E_INTERNAL, SPMV_E_NOMEM. */
+#define SPMV_EMULATE_STATS 8
+spmv_status spmv_plan_emulate(const spmv_csr *A, const spmv_perm *perm,
+                              const spmv_splits *splits, const spmv_opts *opts,
+                              int32_t n_sm, const double *x, double *y, int64_t *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,7 +50,10 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
            "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched", "spmv_features",
            "spmv_mlp_param_count", "spmv_mlp_work_bytes", "spmv_mlp_forward", "spmv_mlp_grad",
-           "spmv_mlp_adam")
+           "spmv_mlp_adam", "spmv_plan_emulate")
+SPMV_EMULATE_STATS = 8
+EMULATE_STATS = ("tiles", "chunk_tiles", "staged_tiles", "partial_slots", "fixups", "warp_rows",
+                 "stored_chunk_elements", "plain_csr")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
@@ -182,12 +185,15 @@ def _load():
                                      ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(vp),
                                      ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_float)]
+    L.spmv_plan_emulate.argtypes = [ctypes.POINTER(spmv_csr), ctypes.POINTER(spmv_perm),
+                                    ctypes.POINTER(spmv_splits), ctypes.POINTER(spmv_opts),
+                                    ctypes.c_int32, vp, vp, vp]
     for name in ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
                  "spmv_unpermute_y", "spmv_plan_get_info", "spmv_plan_destroy",
                  "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
                  "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir",
                  "spmv_plan_create_batched", "spmv_features", "spmv_mlp_forward",
-                 "spmv_mlp_grad", "spmv_mlp_adam"):
+                 "spmv_mlp_grad", "spmv_mlp_adam", "spmv_plan_emulate"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -298,6 +304,35 @@ def spmv_plan_create(m, n, rowptr, colidx, vals, row_perm=None, col_perm=None,
     plan = Plan(handle, None)
     plan.info = spmv_plan_get_info(plan)
     return plan
+
+
+def spmv_plan_emulate(m, n, rowptr, colidx, vals, x, row_perm=None, col_perm=None,
+                      form=SPMV_NATURAL, K=0, row_part_ptr=None, col_part_ptr=None,
+                      nz_part=None, dtype=SPMV_F64, nrhs=1, tile_cols=0, tile_nnz=0,
+                      long_row=0, lanes=0, flags=0, cta_threads=0, warp_rows=0, n_sm=0):
+    """The host image spmv_plan_create would build (for n_sm SMs), evaluated
+    on the host by walking it as the kernels do: (y, stats).  x: (n,) or
+    (n, nrhs) float64 in the original order; y likewise (m rows).  No GPU."""
+    A, keep = _csr_struct(m, n, rowptr, colidx, vals)
+    rperm = None if row_perm is None else _i32(row_perm)
+    cperm = None if col_perm is None else _i32(col_perm)
+    perm = spmv_perm(_ptr(rperm), _ptr(cperm))
+    rpp = None if row_part_ptr is None else _i32(row_part_ptr)
+    cpp = None if col_part_ptr is None else _i32(col_part_ptr)
+    nzp = None if nz_part is None else _i32(nz_part)
+    splits = spmv_splits(form, K, _ptr(rpp), _ptr(cpp), _ptr(nzp))
+    opts = spmv_opts(dtype, nrhs, tile_cols, tile_nnz, long_row, lanes, flags, warp_rows,
+                     cta_threads)
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    if xs.size != n * max(nrhs, 1):
+        raise ValueError("x has %d elements, expected %d" % (xs.size, n * max(nrhs, 1)))
+    y = np.empty((m, nrhs) if xs.ndim == 2 else m, dtype=np.float64)
+    stats = np.zeros(SPMV_EMULATE_STATS, dtype=np.int64)
+    _check(lib.spmv_plan_emulate(ctypes.byref(A), ctypes.byref(perm), ctypes.byref(splits),
+                                 ctypes.byref(opts), int(n_sm),
+                                 ctypes.c_void_p(xs.ctypes.data), ctypes.c_void_p(y.ctypes.data),
+                                 ctypes.c_void_p(stats.ctypes.data)))
+    return y, dict(zip(EMULATE_STATS, stats.tolist()))
 
 
 def spmv_plan_create_batched(mats, perms=None, nz_parts=None, K=0, dtype=SPMV_F64, nrhs=1,
