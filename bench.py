@@ -45,7 +45,12 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-FORMS_SWEEP = ["natural", "random", "sb1024", "db1024", "split4", "split16", "split64", "split256"]
+# natural and random orders run through both the plain CSR kernel and the
+# tiled kernel ("tiled", "rtiled"), so that the gain of a reordering is
+# measured against the same kernel in the original order
+FORMS_SWEEP = ["natural", "random", "tiled", "rtiled", "sb1024", "db1024", "split4", "split16",
+               "split64", "split256"]
+NATURAL_FORMS = ("natural", "random", "tiled", "rtiled")
 MATRICES = {
     "sweep": [("mesh5_1024", lambda: synth.mesh5(1024, seed=0)),
               ("rmat20_d16", lambda: synth.rmat(20, 16, seed=0)),
@@ -115,6 +120,14 @@ WORKLOAD_TEXT = {
                  "SpMV in the chosen dtype; CG with FP64 iterative refinement to 1e-10 "
                  "with FP64 / FP32 / BF16 inner products",
 }
+
+
+def default_forms(workload):
+    return (FORMS_SWEEP if workload == "sweep" else (
+        ["natural", "random", "tiled", "db1024"] if workload == "precision"
+        else ["natural", "tiled", "sb1024"] if workload == "scale"
+        else ["natural", "batch_split16"] if workload == "batching"
+        else ["natural", "tiled", "sb8", "split16"]))
 
 
 def compulsory_bytes(m, n, nnz, vb=8, xb=8, r=1):
@@ -211,9 +224,12 @@ def form_kwargs(S, f, rp, ci, parts, seed=0):
         return {}, None
     if f == "tiled":
         return dict(flags=S.SPMV_FLAG_TILED_NATURAL), None
-    if f == "random":
+    if f in ("random", "rtiled"):
         p = synth.random_perm(m, 1000 + seed)
-        return dict(row_perm=p, col_perm=p), None
+        kw = dict(row_perm=p, col_perm=p)
+        if f == "rtiled":
+            kw["flags"] = S.SPMV_FLAG_TILED_NATURAL
+        return kw, None
     if f.startswith("sb") or f.startswith("db"):
         r = parts[("cn" if f.startswith("sb") else "ercn", int(f[2:]))]
         return dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"], K=r["K"],
@@ -250,6 +266,18 @@ def tile_shapes(S, dtype, nrhs, nnz):
             "cta256s": dict(dtype=dtype, nrhs=nrhs, flags=S.SPMV_FLAG_STAGE),
             "cta1024": dict(dtype=dtype, nrhs=nrhs, cta_threads=1024),
             "cta256x8": dict(dtype=dtype, nrhs=nrhs, tile_nnz=max(1024, nnz // (8 * 912)))}
+
+
+def err_ratio(y, y_ref, absax):
+    """max_i |y - y_ref|_i / (|A||x|)_i (inf where |A||x| is 0 and y differs);
+    NaN entries (unwritten output) fail."""
+    y, y_ref, absax = (np.asarray(a, dtype=np.float64).reshape(-1) for a in (y, y_ref, absax))
+    if np.any(np.isnan(y)):
+        raise RuntimeError("unwritten output entries")
+    err = np.abs(y - y_ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where(absax > 0, err / absax, np.where(err > 0, np.inf, 0.0))
+    return float(ratio.max()) if ratio.size else 0.0
 
 
 def library_reference(S, m, n, rp, ci, v, x64):
@@ -379,30 +407,80 @@ def ncu_traffic(label, kernel):
 
 
 # ------------------------------------------------------------- reference --
+def _plain_prepared(mats):
+    """The matrices in the arrays the oracle's plain loop reads (no
+    conversion inside a timed call) with x ~ U(-1, 1)."""
+    return [(name, len(rp) - 1, np.ascontiguousarray(rp, dtype=np.int64),
+             np.ascontiguousarray(ci, dtype=np.int32), np.ascontiguousarray(v, dtype=np.float64),
+             synth.uniform_x(len(rp) - 1, 1)) for name, rp, ci, v in mats]
+
+
+def plain_cpu_gbs(prepared, threads, budget_s, reps=5):
+    """The oracle's plain FP64 CSR loop (Sec. 2.1) on the host, the paper's
+    protocol (3 warm-up calls, then timed calls; Sec. 5.2) per matrix: `reps`
+    repetitions of `calls` calls, the median repetition.  GB/s = compulsory
+    bytes of one product of every matrix / the sum of the matrices' median
+    times per call.  `calls` is sized so that the whole measurement takes
+    about budget_s seconds."""
+    import oracle
+    t_call, b_tot = 0.0, 0
+    per = []
+    for name, m, rp, ci, v, x in prepared:
+        y = np.empty(m, dtype=np.float64)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            oracle.spmv_plain(m, rp, ci, v, x, threads, out=y)
+        est = (time.perf_counter() - t0) / 3
+        calls = int(max(1, min(100, budget_s / (len(prepared) * reps * max(est, 1e-6)))))
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            for _ in range(calls):
+                oracle.spmv_plain(m, rp, ci, v, x, threads, out=y)
+            ts.append((time.perf_counter() - t0) / calls)
+        t_call += float(np.median(ts))
+        b_tot += compulsory_bytes(m, m, int(rp[-1]))
+        per.append("%s %d x %d calls" % (name, reps, calls))
+    return b_tot / t_call / 1e9, per
+
+
+def cpu_threads():
+    import oracle
+    return max(1, min(os.cpu_count() or 1, oracle.plain_max_threads()))
+
+
 def run_reference(args, rank, world):
-    """The CPU oracle (single-threaded FP64 compensated SpMV) timed on the
-    host, one whole-matrix SpMV per step, cycling through the matrices."""
+    """The reference arm: the oracle's plain FP64 CSR loop (Sec. 2.1) on the
+    host's cores (OpenMP), on the same (matrix, form) units as this library's
+    step.  Every form computes the same product y = A x, which the oracle
+    computes on the matrix in its original order; one step = one product per
+    unit of the step."""
     if rank != 0:
         return
     import oracle
     mats = make_matrices(args.workload, None, args.matrices.split(",") if args.matrices else None)
-    prepared = [(name, rp.astype(np.int64), ci, v, synth.uniform_x(len(rp) - 1, 1))
-                for name, rp, ci, v in mats]
+    prepared = _plain_prepared(mats)
+    forms = args.forms.split(",") if args.forms else default_forms(args.workload)
+    threads = cpu_threads()
+    units = [(p, f) for p in prepared for f in forms]
     for w in range(args.warmup):
-        name, rp, ci, v, x = prepared[w % len(prepared)]
-        oracle.spmv(len(rp) - 1, len(rp) - 1, rp, ci, v, x)
-    tot_bytes, tot_flops, t = 0, 0, 0.0
+        name, m, rp, ci, v, x = units[w % len(units)][0]
+        oracle.spmv_plain(m, rp, ci, v, x, threads)
+    ys = {p[0]: np.empty(p[1], dtype=np.float64) for p in prepared}
+    step_bytes = sum(compulsory_bytes(p[1], p[1], int(p[2][-1])) for p, _ in units)
+    step_flops = sum(2 * int(p[2][-1]) for p, _ in units)
+    ts = []
     for s in range(args.steps):
-        name, rp, ci, v, x = prepared[s % len(prepared)]
-        m = len(rp) - 1
         t0 = time.perf_counter()
-        oracle.spmv(m, m, rp, ci, v, x)
-        t += time.perf_counter() - t0
-        tot_bytes += compulsory_bytes(m, m, int(rp[-1]))
-        tot_flops += 2 * int(rp[-1])
-    gbs = tot_bytes / t / 1e9
-    sample = ("%d FP64 oracle SpMVs (compensated sums, 1 thread), one whole matrix per step "
-              "cycling %s" % (args.steps, "/".join(p[0] for p in prepared)))
+        for (name, m, rp, ci, v, x), _ in units:
+            oracle.spmv_plain(m, rp, ci, v, x, threads, out=ys[name])
+        ts.append(time.perf_counter() - t0)
+    t = float(np.sum(ts))
+    gbs = step_bytes * args.steps / t / 1e9
+    sample = ("oracle's plain FP64 CSR loop, OpenMP over %d host threads (nproc %d): %d steps of "
+              "%d products (one per (matrix, form) unit: %s x %s), each on the matrix in "
+              "original order" % (threads, os.cpu_count() or 0, args.steps, len(units),
+                                  "/".join(p[0] for p in prepared), ",".join(forms)))
     line = {
         "impl": "reference", "metric": "SpMV GB/s (compulsory bytes; % of GB300 HBM roofline)",
         "value": round(gbs, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -410,55 +488,47 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload],
-                   "matrices": [p[0] for p in prepared],
-                   "unit_of_work": "one y<-Ax of one whole matrix per step, the matrices in turn "
-                                   "(every form of the method computes this same product)",
-                   "nrhs": 1, "parallelism": "1 host thread"},
-        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                   "matrices": [p[0] for p in prepared], "forms": forms,
+                   "unit_of_work": "one y<-Ax per (matrix, form) per step; every form computes "
+                                   "the same product, which the oracle computes in original "
+                                   "order",
+                   "nrhs": 1, "parallelism": "%d host threads" % threads},
+        "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
-        "gflops": round(tot_flops / t / 1e9, 3),
+        "gflops": round(step_flops * args.steps / t / 1e9, 3),
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_sample(mats, budget_s):
-    """The oracle on the host on a bounded sample: whole-matrix SpMVs, cycling
-    through the workload's matrices until about budget_s seconds."""
-    import oracle
-    t_tot, b_tot, count, names = 0.0, 0, 0, []
-    while count < 3 * len(mats) and (t_tot < budget_s or count < len(mats)):
-        name, rp, ci, v = mats[count % len(mats)]
-        m = len(rp) - 1
-        x = synth.uniform_x(m, 1)
-        rp64 = rp.astype(np.int64)
-        t0 = time.perf_counter()
-        oracle.spmv(m, m, rp64, ci, v, x)
-        t_tot += time.perf_counter() - t0
-        b_tot += compulsory_bytes(m, m, int(rp[-1]))
-        count += 1
-        names.append(name)
-    return {"value": round(b_tot / t_tot / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "%d FP64 oracle SpMVs (compensated sums, 1 thread): %s"
-                      % (count, ",".join(names))}
+    """The oracle's plain FP64 CSR loop on the host (Sec. 2.1; the paper's
+    protocol of warm-up calls and timed calls, median of 5 repetitions), on
+    every matrix of the workload in its original order: single-threaded and
+    with OpenMP over all host cores.  `value` is the all-cores figure."""
+    prepared = _plain_prepared(mats)
+    threads = cpu_threads()
+    one, per1 = plain_cpu_gbs(prepared, 1, budget_s / 2)
+    allc, per = plain_cpu_gbs(prepared, threads, budget_s / 2)
+    return {"value": round(allc, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": "oracle's plain FP64 CSR loop (Sec. 2.1) on each matrix in original order, "
+                      "3 warm-ups then 5 repetitions, median; OpenMP over %d threads: %s"
+                      % (threads, "; ".join(per)),
+            "single_thread": {"value": round(one, 3), "unit": "GB/s", "cores": 1,
+                              "sample": "; ".join(per1)}}
 
 
 # ------------------------------------------------------------------- ours --
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1203_2739_gb300 as S
-    from tests._util import err_ratio
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     log = (lambda s: print(s, file=sys.stderr, flush=True)) if rank == 0 else (lambda s: None)
-    forms = args.forms.split(",") if args.forms else (
-        FORMS_SWEEP if args.workload == "sweep" else (
-            ["natural", "random", "db1024"] if args.workload == "precision"
-            else ["natural", "sb1024"] if args.workload == "scale"
-            else ["natural", "batch_split16"] if args.workload == "batching"
-            else ["natural", "sb8", "split16"]))
+    forms = args.forms.split(",") if args.forms else default_forms(args.workload)
     dtype = {"f64": S.SPMV_F64, "f32": S.SPMV_F32, "bf16": S.SPMV_BF16}[args.dtype]
     vb, xb = {0: (8, 8), 1: (4, 4), 2: (2, 4)}[dtype]
     tdt = torch.float64 if dtype == S.SPMV_F64 else torch.float32
@@ -571,7 +641,7 @@ def run_ours(args, rank, world, local_rank):
         hy = [torch.empty(e["yh"].numel(), dtype=e["yh"].dtype).pin_memory() for e in entries]
         for i, e in enumerate(entries):
             S.spmv_exec_host(e["plan"], hx[i], hy[i])
-        e2e_steps = max(1, min(args.steps, 5))
+        e2e_steps = max(1, min(args.steps, 20))
         ta = time.perf_counter()
         for _ in range(e2e_steps):
             for i, e in enumerate(entries):
@@ -619,14 +689,7 @@ def run_ours(args, rank, world, local_rank):
             "launches": e["info"]["launches_per_exec"], "tile_shape": e["tile_shape"],
             "moved_over_compulsory": round(e["info"]["moved_bytes"] / e["bytes"], 3),
             "bound_cost": e["cost"]}
-    best = {}
-    for label, dd in detail.items():
-        mat, form = label.split("/")
-        if mat not in best or dd["us"] < best[mat][1]:
-            best[mat] = (form, dd["us"])
-    speedup = {mat: {"best_form": best[mat][0],
-                     "speedup_vs_natural": round(detail[mat + "/natural"]["us"] / best[mat][1], 3)
-                     if (mat + "/natural") in detail else None} for mat in best}
+    speedup = reorder_gains(detail)
     # the paper's Table 3 analogue: partitioning time on the host, and the
     # number of products after which a form has paid for it against plain
     # CSR in natural order
@@ -672,6 +735,36 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(mats, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+def reorder_gains(detail):
+    """Per matrix: the fastest form; its speedup over plain CSR in natural
+    order and over the faster of the two natural-order kernels (plain CSR,
+    tiled); and, the paper's comparison (Table 2: each method's time against
+    the original order), each reordered or split form's gain over the same
+    tiled kernel in natural order (and random order's, for contrast)."""
+    out = {}
+    mats = []
+    for label in detail:
+        mat = label.split("/")[0]
+        if mat not in mats:
+            mats.append(mat)
+    for mat in mats:
+        us = {label.split("/")[1]: dd["us"] for label, dd in detail.items()
+              if label.split("/")[0] == mat}
+        best_form = min(us, key=us.get)
+        nat = [us[f] for f in ("natural", "tiled") if f in us]
+        e = {"best_form": best_form,
+             "speedup_vs_natural": round(us["natural"] / us[best_form], 3)
+             if "natural" in us else None,
+             "speedup_vs_best_natural_kernel": round(min(nat) / us[best_form], 3)
+             if nat else None}
+        if "tiled" in us:
+            e["gain_over_tiled_natural"] = {
+                f: round(us["tiled"] / t, 3) for f, t in us.items()
+                if f not in ("natural", "random", "tiled")}
+        out[mat] = e
+    return out
 
 
 def graph_replay(S, e, stream, iters=100, reps=5):

@@ -416,9 +416,16 @@ const char *spmv_last_error(void);
  * into the library (2 * SPMV_NOALLOC_MAX_NNZ / 4096 doubles = 4 MiB, held on
  * every device that loads the library until the process exits).
  *   - nnz > SPMV_NOALLOC_MAX_NNZ is rejected with SPMV_E_UNSUPPORTED.
- *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before capturing the stream into a graph.
+ *   - The first call on a device sets the entry point up with that device
+ *     current: it looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) and loads this entry point's kernels.  CUDA
+ *     loads modules lazily by default, so this first call is the one that
+ *     places the scratch array and the kernels' code in device memory, and
+ *     it can fail with SPMV_E_CUDA when the device is out of memory.  Make it
+ *     at set-up time, before the code that cannot allocate and before any
+ *     stream capture: a call with m = 0 (every pointer may then be NULL)
+ *     does the set-up and nothing else.  Later calls on that device allocate
+ *     nothing.
  *   - Every call shares the one scratch array and overwrites what it uses:
  *     calls whose kernels overlap on the GPU (different streams, threads)
  *     race and must be serialised by the caller.

@@ -10,6 +10,8 @@ What each function restates (the C file ``ref.c`` holds the loops):
 
 * ``spmv``            y = A x from the CSR definition (Sec. 2.1), Neumaier
                       compensated FP64 sums; also returns (|A||x|)_i.
+* ``spmv_plain``      the plain CSR loop of Sec. 2.1 (the timed CPU baseline,
+                      OpenMP over the host's cores when built with it).
 * ``permute``         A_hat = P_r A P_c (Sec. 3).
 * ``form_rows``       SB form, eqs. (1)-(3); DB form, eq. (5), from row labels.
 * ``form_split``      row/column order of a split by first-touching part (Sec. 4).
@@ -55,6 +57,10 @@ def lib():
         L = ctypes.CDLL(path)
         L.ref_spmv.argtypes = [_i32, _i64p, _i32p, _f64p, _f64p, _i32, _f64p, ctypes.c_void_p]
         L.ref_spmv.restype = None
+        L.ref_spmv_plain.argtypes = [_i32, _i64p, _i32p, _f64p, _f64p, _f64p, _i32]
+        L.ref_spmv_plain.restype = None
+        L.ref_plain_max_threads.argtypes = []
+        L.ref_plain_max_threads.restype = _i32
         L.ref_is_perm.argtypes = [_i32, _i32p]
         L.ref_is_perm.restype = _i32
         L.ref_permute_csr.argtypes = [_i32, _i32, _i64p, _i32p, _f64p, _i32p, _i32p,
@@ -112,6 +118,21 @@ def spmv(m, n, rowptr, colidx, vals, x):
     lib().ref_spmv(m, rp, ci, v, x.reshape(-1), r, y.reshape(-1),
                    a.ctypes.data_as(ctypes.c_void_p))
     return y, a
+
+
+def spmv_plain(m, rowptr, colidx, vals, x, threads=1, out=None):
+    """The plain CSR loop of Sec. 2.1 (one FP64 running sum per row, no
+    compensation): the timed CPU baseline.  threads > 1 uses OpenMP when the
+    oracle was built with it.  rowptr must already be int64, colidx int32 and
+    vals / x float64 (no conversion inside the timed call)."""
+    y = np.empty(m, dtype=np.float64) if out is None else out
+    lib().ref_spmv_plain(m, rowptr, colidx, vals, x, y, int(threads))
+    return y
+
+
+def plain_max_threads():
+    """Threads spmv_plain can use (1 when the oracle was built without OpenMP)."""
+    return int(lib().ref_plain_max_threads())
 
 
 def spmv_rows(rowptr, colidx, vals, x, rows):

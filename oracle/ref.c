@@ -10,6 +10,10 @@
  * Every function cites the passage of the paper it restates:
  *   ref_spmv            y = A x by the CSR definition (Sec. 2.1, Sec. 1),
  *                       compensated (Neumaier) FP64 sums, plus (|A||x|)_i.
+ *   ref_spmv_plain      the same product as the paper's plain CSR loop
+ *                       (Sec. 2.1: one FP64 running sum per row), the timed
+ *                       CPU baseline; with OpenMP (when the build has it) the
+ *                       rows are shared among host threads.
  *   ref_permute_csr     A_hat = P_r A P_c (Sec. 3, first paragraph).
  *   ref_form_rows       SB form (eqs. 1-3) / DB form (eq. 5) from row labels.
  *   ref_form_split      row/column order of a split (Sec. 4) by first-touching part.
@@ -27,6 +31,9 @@
  *                       the gradients by the chain rule, in FP64.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -60,6 +67,35 @@ void ref_spmv(int32_t m, const int64_t *rowptr, const int32_t *col,
 }
 
 /* ------------------------------------------------------- permutations --- */
+
+/* The plain CSR SpMxV of Sec. 2.1: for each row, one FP64 running sum over
+ * its nonzeros in storage order, written to y.  No compensation: this is the
+ * loop whose speed the CPU baseline reports, not a checker.  threads > 1
+ * shares the rows among that many OpenMP threads (static schedule) when the
+ * oracle was built with OpenMP; the sums are the same either way. */
+void ref_spmv_plain(int32_t m, const int64_t *rowptr, const int32_t *col,
+                    const double *val, const double *x, double *y, int32_t threads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (int32_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s += val[p] * x[col[p]];
+        y[i] = s;
+    }
+    (void)threads;
+}
+
+/* Host threads ref_spmv_plain can use: OpenMP's maximum, 1 without OpenMP. */
+int32_t ref_plain_max_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 int32_t ref_is_perm(int32_t n, const int32_t *perm)
 {

@@ -132,6 +132,19 @@ bool run_tile(Emu &E, const Tile &t)
     E.n_win = t.runlen + t.listlen;
     if (t.runlen < 0 || t.listlen < 0) return E.fail("window lengths", t.runlen, t.listlen);
     if (t.kind == TILE_NARROW && E.n_win > 65536) return E.fail("narrow window", E.n_win, 0);
+    // the device's preconditions: the window fits the dynamic shared memory
+    // the launch reserves (max_staged entries), and the bulk copy of the
+    // run's 16-byte body starts on a 16-byte boundary of x_hat
+    if (E.n_win > P.max_staged) return E.fail("window beyond the reserved shared memory",
+                                              E.n_win, P.max_staged);
+    {
+        const int64_t xb = P.dtype == SPMV_F64 ? 8 : 4;
+        const int64_t body = ((int64_t)t.runlen * r * xb) & ~(int64_t)15;
+        if (body > 0 && ((int64_t)t.run0 * r * xb) % 16 != 0)
+            return E.fail("bulk copy source not 16-byte aligned", t.run0, r);
+        if ((int64_t)P.max_staged * r * xb > 227 * 1024)
+            return E.fail("reserved shared memory beyond 227 KB", P.max_staged, r);
+    }
     E.win.assign((size_t)E.n_win * r, 0.0);
     for (int32_t i = 0; i < t.runlen; ++i) {
         const int64_t g = (int64_t)t.run0 + i;

@@ -109,6 +109,9 @@ __global__ void k_noalloc_zero(int32_t m, double *__restrict__ y)
 
 // Device address of the scratch array, looked up once per device with that
 // device current (in host code the array's name is only a host-side handle).
+// CUDA loads modules lazily by default: the lookup loads this file's module
+// (and with it the scratch array) onto the device, and cudaFuncGetAttributes
+// loads each kernel's code, so that no later call has to allocate for them.
 std::mutex g_mu;
 double *g_scratch_ptr[128] = {nullptr};
 
@@ -131,6 +134,17 @@ spmv_status scratch_for_current_device(double **out)
         if (e != cudaSuccess) {
             set_error("cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
             return SPMV_E_CUDA;
+        }
+        const void *kernels[] = {reinterpret_cast<const void *>(k_noalloc_chunks),
+                                 reinterpret_cast<const void *>(k_noalloc_fixup),
+                                 reinterpret_cast<const void *>(k_noalloc_zero)};
+        for (const void *k : kernels) {
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, k);
+            if (e != cudaSuccess) {
+                set_error("loading the kernels of this entry point: %s", cudaGetErrorString(e));
+                return SPMV_E_CUDA;
+            }
         }
         g_scratch_ptr[dev] = static_cast<double *>(p);
     }
@@ -159,14 +173,15 @@ extern "C" spmv_status spmv_csr_exec_noalloc(int32_t m, int32_t n, int64_t nnz,
                   (long long)nnz, (long long)SPMV_NOALLOC_MAX_NNZ);
         return SPMV_E_UNSUPPORTED;
     }
+    // set-up first: a call with m = 0 does only this (see the header)
+    double *scratch = nullptr;
+    spmv_status st = scratch_for_current_device(&scratch);
+    if (st != SPMV_OK) return st;
     if (m == 0) return SPMV_OK;
     if (!rowptr_dev || !y_dev || (nnz > 0 && (!colidx_dev || !vals_dev || !x_dev))) {
         set_error("NULL argument");
         return SPMV_E_INVALID;
     }
-    double *scratch = nullptr;
-    spmv_status st = scratch_for_current_device(&scratch);
-    if (st != SPMV_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (nnz == 0) {
         k_noalloc_zero<<<(unsigned)((m + kNoallocThreads - 1) / kNoallocThreads), kNoallocThreads,

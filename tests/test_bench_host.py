@@ -198,8 +198,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["value"] > 0
     assert d["config"]["workload"] == bench.WORKLOAD_TEXT["zipf16k"]
     assert d["config"]["matrices"] == ["zipf16k"]
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == bench.cpu_threads()
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["config"]["forms"] == bench.default_forms("zipf16k")
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     sel = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
@@ -248,3 +250,30 @@ def test_library_reference_is_y_and_abs_product(nrhs):
         got_abs = absax if nrhs == 1 else absax[:, c]
         assert np.allclose(got, want, rtol=1e-13, atol=1e-13)
         assert np.allclose(got_abs, want_abs, rtol=1e-13, atol=1e-13)
+
+
+def test_cpu_baseline_is_plain_loop_single_and_all_cores():
+    """The CPU baseline times the oracle's plain CSR loop on one thread and on
+    every host core, median of 5 repetitions, and says how many it used."""
+    mats = [("z", *synth.zipf_matrix(2048, 2048, seed=0))]
+    d = bench.cpu_baseline_sample(mats, budget_s=0.5)
+    assert d["kind"] == "oracle" and d["unit"] == "GB/s" and d["value"] > 0
+    assert d["cores"] == bench.cpu_threads() and d["nproc"] == os.cpu_count()
+    assert d["single_thread"]["cores"] == 1 and d["single_thread"]["value"] > 0
+    assert "5 x" in d["sample"] and "plain" in d["sample"]
+
+
+def test_reorder_gains_use_the_same_kernel_in_natural_order():
+    detail = {"a/natural": {"us": 10.0}, "a/tiled": {"us": 8.0}, "a/random": {"us": 20.0},
+              "a/rtiled": {"us": 16.0}, "a/sb1024": {"us": 4.0}, "a/split4": {"us": 5.0}}
+    g = bench.reorder_gains(detail)["a"]
+    assert g["best_form"] == "sb1024"
+    assert g["speedup_vs_natural"] == 2.5
+    assert g["speedup_vs_best_natural_kernel"] == 2.0
+    assert g["gain_over_tiled_natural"] == {"rtiled": 0.5, "sb1024": 2.0, "split4": 1.6}
+
+
+def test_err_ratio_flags_unwritten_entries():
+    assert bench.err_ratio([1.0, 2.0], [1.0, 2.5], [1.0, 1.0]) == 0.5
+    with pytest.raises(RuntimeError):
+        bench.err_ratio([float("nan")], [0.0], [1.0])

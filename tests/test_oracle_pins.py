@@ -50,6 +50,25 @@ def test_spmv_equals_dense_matvec_exactly(seed, shape):
     assert np.array_equal(Y, A @ X)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_plain_loop_equals_dense_matvec_exactly(seed):
+    """The timed plain CSR loop (Sec. 2.1) is the dense product by brute force
+    with exact integer data, on one thread and on every host thread; and it
+    is a running left-to-right sum (1e16 + 1 - 1e16 gives 0, where the
+    compensated checker gives 1)."""
+    m, n = 300, 211
+    rp, ci, v = synth.random_sparse(m, n, 0.1, seed, integer=True, empty_rows=0.2)
+    A = _dense(m, n, rp, ci, v)
+    x = synth.integer_x(n, seed + 1)
+    rp64 = np.ascontiguousarray(rp, dtype=np.int64)
+    for threads in (1, oracle.plain_max_threads()):
+        y = oracle.spmv_plain(m, rp64, np.ascontiguousarray(ci, dtype=np.int32), v, x, threads)
+        assert np.array_equal(y, A @ x)
+    y = oracle.spmv_plain(1, np.array([0, 3], dtype=np.int64), np.array([0, 1, 2], np.int32),
+                          np.array([1e16, 1.0, -1e16]), np.ones(3))
+    assert y[0] == 0.0
+
+
 def test_spmv_sums_are_compensated():
     """The oracle's row sums carry a running error term (Neumaier), so
     cancellation that a plain left-to-right FP64 sum gets wrong comes out
@@ -349,6 +368,91 @@ def test_lru_compulsory_misses_when_everything_fits(seed):
     assert out["val"] == nnz
     assert out["col"] == (nnz + 1) // 2 if nnz else True
     assert out["rowptr"] == 26          # 51 four-byte entries over 8-byte lines
+
+
+def _gcsr_trace(part_rows, gptr, gcol, drop_y=False):
+    """The access order of the multiple SpMxV over GCSR parts (Sec. 4, GCSR
+    Sec. 5.2), written out: per stored row t its row-list entry, its two row
+    starts, per nonzero its column index, value and x entry, then its y
+    entry; (array id, element, element bytes) with the simulator's array ids
+    (0 rowptr, 1 col, 2 val, 3 x, 4 y, 5 rowlist)."""
+    tr = []
+    for t in range(len(part_rows)):
+        tr += [(5, t, 4), (0, t, 4), (0, t + 1, 4)]
+        for q in range(int(gptr[t]), int(gptr[t + 1])):
+            tr += [(1, q, 4), (2, q, 8), (3, int(gcol[q]), 8)]
+        if not drop_y:
+            tr.append((4, int(part_rows[t]), 8))
+    return tr
+
+
+def _textbook_replay(trace, lines, line_bytes):
+    from collections import OrderedDict
+    cache, misses = OrderedDict(), np.zeros(6, dtype=np.int64)
+    for a, i, es in trace:
+        key = (a, i * es // line_bytes)
+        if key in cache:
+            cache.move_to_end(key)
+            continue
+        misses[a] += 1
+        cache[key] = True
+        if len(cache) > lines:
+            cache.popitem(last=False)
+    return misses
+
+
+def test_gcsr_lru_golden_trace():
+    """A hand-worked GCSR replay (tests/golden/lru_traces.json)."""
+    g = _golden("lru_traces.json")["gcsr"]
+    for c in g["cases"]:
+        out = oracle.cachesim_gcsr(g["part_rows"], g["gcsr_ptr"], g["gcsr_col"],
+                                   c["lines"] * c["line_bytes"], c["line_bytes"])
+        got = [out[k] for k in oracle.ARRAYS]
+        assert got == c["misses"], c
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_gcsr_lru_compulsory_misses_when_everything_fits(seed):
+    """With a cache larger than everything the replay touches, each array
+    misses once per distinct line: row list ceil(4T/L), row starts
+    ceil(4(T+1)/L), columns ceil(4 nnz/L), values ceil(8 nnz/L), x and y the
+    distinct lines of the columns and rows touched."""
+    m, n, K = 70, 90, 4
+    rp, ci, v = synth.random_sparse(m, n, 0.08, seed)
+    nnz = int(rp[-1])
+    part = synth.random_labels(nnz, K, seed + 3)
+    prp, prows, gptr, pos = oracle.split_parts(m, rp, K, part)
+    gcol = ci[pos]
+    T = len(prows)
+    for L in (8, 64):
+        out = oracle.cachesim_gcsr(prows, gptr, gcol, 1 << 22, L)
+        assert out["rowlist"] == -(-4 * T // L)
+        assert out["rowptr"] == -(-4 * (T + 1) // L)
+        assert out["col"] == -(-4 * nnz // L)
+        assert out["val"] == -(-8 * nnz // L)
+        assert out["x"] == len({8 * int(c) // L for c in gcol})
+        assert out["y"] == len({8 * int(i) // L for i in prows})
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_gcsr_lru_matches_the_written_out_access_order(seed):
+    """The C replay against the access order of Sec. 4 written out in Python
+    and an ordered-dict LRU, for several capacities and line sizes; the same
+    comparison tells a replay that drops the y accesses apart."""
+    m, n, K = 60, 50, 5
+    rp, ci, v = synth.random_sparse(m, n, 0.1, seed)
+    nnz = int(rp[-1])
+    part = synth.random_labels(nnz, K, seed + 1)
+    prp, prows, gptr, pos = oracle.split_parts(m, rp, K, part)
+    gcol = ci[pos]
+    tr = _gcsr_trace(prows, gptr, gcol)
+    no_y = _gcsr_trace(prows, gptr, gcol, drop_y=True)
+    for L in (8, 64):
+        for lines in (1, 3, 16, 200):
+            out = oracle.cachesim_gcsr(prows, gptr, gcol, lines * L, L)
+            got = np.array([out[k] for k in oracle.ARRAYS])
+            assert np.array_equal(got, _textbook_replay(tr, lines, L)), (L, lines)
+            assert not np.array_equal(got, _textbook_replay(no_y, lines, L)), (L, lines)
 
 
 def _sb_parts_sizes(m, n, rp, ci, K, labels):

@@ -4,9 +4,12 @@ It is meant for callers that cannot allocate device memory when they need a
 product -- code running inside a memory pool it does not own, a plugin handed
 only its buffers, a step that must leave the allocator alone.  Its partial
 sums live in a fixed scratch array compiled into the library.  Here its output
-is checked, through the C ABI, against the planned entry point (spmv_exec on a
-natural-order FP64 plan) on two calls in a row, with the FP64 tolerance of the
-other tests.  This file is collected last on purpose."""
+is checked, through the C ABI, against the CPU oracle's y and |A||x| with the
+FP64 tolerance of the other tests, and against the planned entry point
+(spmv_exec on a natural-order FP64 plan), on two calls in a row; after the
+set-up call, the free device memory and torch's allocated bytes must not
+change across calls.  This file is collected last, so that a run stopping at
+its first failure has run every other test first."""
 import ctypes
 
 import numpy as np
@@ -32,7 +35,8 @@ def _matrix():
     return (m, n) + synth.coo_to_csr(m, n, rows, cols, vals)
 
 
-def test_noalloc_matches_planned_entry_point_two_calls():
+def test_noalloc_matches_oracle_and_planned_entry_point_two_calls():
+    import oracle
     import paper_1203_2739_gb300 as S
     torch.cuda.set_device(0)
     m, n, rp, ci, v = _matrix()
@@ -42,21 +46,31 @@ def test_noalloc_matches_planned_entry_point_two_calls():
     d_rp = torch.from_numpy(rp).cuda()
     d_ci = torch.from_numpy(ci).cuda()
     d_v = torch.from_numpy(v).cuda()
-    absA = torch.from_numpy(np.abs(v)).cuda()
-    for call, seed in enumerate((1, 2)):
-        x = torch.from_numpy(synth.uniform_x(n, seed)).cuda()
-        y_plan = torch.empty(m, dtype=torch.float64, device="cuda")
-        y_noalloc = torch.full((m,), float("nan"), dtype=torch.float64, device="cuda")
-        absax = torch.empty_like(y_plan)
-        S.spmv_exec(plan, x, y_plan)
-        S.spmv_csr_exec_noalloc(m, n, d_rp, d_ci, d_v, x, y_noalloc)
-        # |A||x| through the same entry point, for the tolerance
-        S.spmv_csr_exec_noalloc(m, n, d_rp, d_ci, absA, x.abs(), absax)
+    xs = [synth.uniform_x(n, seed) for seed in (1, 2)]
+    dx = [torch.from_numpy(x).cuda() for x in xs]
+    y_plan = torch.empty(m, dtype=torch.float64, device="cuda")
+    y_noalloc = torch.empty(m, dtype=torch.float64, device="cuda")
+    # set-up call (m = 0): loads the entry point's module and kernels
+    assert S.lib.spmv_csr_exec_noalloc(0, 0, 0, None, None, None, None, None, None) == S.SPMV_OK
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for call, (x, xd) in enumerate(zip(xs, dx)):
+        y_noalloc.fill_(float("nan"))
+        S.spmv_csr_exec_noalloc(m, n, d_rp, d_ci, d_v, xd, y_noalloc)
         torch.cuda.synchronize()
-        a, b, s = y_plan.cpu().numpy(), y_noalloc.cpu().numpy(), absax.cpu().numpy()
+        assert torch.cuda.mem_get_info()[0] == free0, "call %d changed free device memory" % call
+        assert torch.cuda.memory_allocated() == alloc0, "call %d allocated through torch" % call
+        S.spmv_exec(plan, xd, y_plan)
+        torch.cuda.synchronize()
+        b = y_noalloc.cpu().numpy()
         assert not np.isnan(b).any(), "call %d left entries unwritten" % call
-        err = np.abs(a - b)
-        assert np.all(err <= TOL[S.SPMV_F64] * s), (call, float((err / np.maximum(s, 1e-300)).max()))
+        y_ref, absax = oracle.spmv(m, n, rp, ci, v, x)
+        tol = TOL[S.SPMV_F64] * absax
+        err = np.abs(b - y_ref)
+        assert np.all(err <= tol), (call, float((err / np.maximum(absax, 1e-300)).max()))
+        # and the planned entry point, held to the same oracle
+        assert np.all(np.abs(y_plan.cpu().numpy() - y_ref) <= tol), call
+    S.spmv_plan_destroy(plan)
 
 
 def test_noalloc_edges_and_limit():
