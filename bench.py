@@ -183,8 +183,7 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     if cache_dir:
         for key in list(need):
             if os.path.exists(path(key)):
-                with np.load(path(key)) as z:
-                    res[key] = {k: (z[k] if z[k].ndim else z[k].item()) for k in z.files}
+                res[key] = load_partition(S, path(key), m, n, rp, ci)
                 del need[key]
     if not need:
         return res
@@ -196,8 +195,30 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
             res[key] = fu.result()
             if cache_dir:
                 os.makedirs(cache_dir, exist_ok=True)
-                np.savez(path(key), **res[key])
+                save_partition(path(key), res[key])
     return res
+
+
+def save_partition(path, r):
+    """Keep a partition as its labels (the smallest integer type that holds
+    them, compressed) and its scalars; the form is derived again on load."""
+    lab = np.asarray(r["labels"])
+    dt = np.uint8 if r["K"] < 256 else (np.uint16 if r["K"] < 65535 else np.int32)
+    np.savez_compressed(path, labels=lab.astype(dt), form=r["form"], K=r["K"], cost=r["cost"],
+                        cost_cols=r["cost_cols"], cost_rows=r["cost_rows"],
+                        seconds=r["seconds"])
+
+
+def load_partition(S, path, m, n, rp, ci):
+    """A partition kept by save_partition, with its form rebuilt from the
+    labels exactly as spmv_partition derives it (spmv_form_from_labels)."""
+    with np.load(path) as z:
+        r = {k: z[k].item() for k in z.files if k != "labels"}
+        lab = np.ascontiguousarray(z["labels"], dtype=np.int32)
+    rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, int(r["form"]), int(r["K"]),
+                                                     lab)
+    r.update(labels=lab, row_perm=rperm, col_perm=cperm, row_part_ptr=rpp, col_part_ptr=cpp)
+    return r
 
 
 def batched_split_plan(S, name, K, dtype, threads, nrhs=1):
@@ -258,12 +279,14 @@ def form_kwargs(S, f, rp, ci, parts, seed=0):
 def tile_shapes(S, dtype, nrhs, nnz):
     """The launch shapes the autotuner chooses from for a tiled plan: one
     wave of 256-thread tiles (rows over 64, or over 128, nonzeros reduced by
-    a warp; or staging x), wide 1024-thread tiles, or eight waves of smaller
-    tiles (launched in order, so that the x windows of the tiles running at
-    once stay within L2 when x does not)."""
+    a warp; or staging x), 512-thread tiles (two per SM, 96 KB windows),
+    wide 1024-thread tiles (one per SM, 200 KB windows), or eight waves of
+    smaller tiles (launched in order, so that the x windows of the tiles
+    running at once stay within L2 when x does not)."""
     return {"cta256": dict(dtype=dtype, nrhs=nrhs),
             "cta256w": dict(dtype=dtype, nrhs=nrhs, warp_rows=128),
             "cta256s": dict(dtype=dtype, nrhs=nrhs, flags=S.SPMV_FLAG_STAGE),
+            "cta512": dict(dtype=dtype, nrhs=nrhs, cta_threads=512),
             "cta1024": dict(dtype=dtype, nrhs=nrhs, cta_threads=1024),
             "cta256x8": dict(dtype=dtype, nrhs=nrhs, tile_nnz=max(1024, nnz // (8 * 912)))}
 
@@ -990,8 +1013,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="tiled forms with the default tile shape instead of the autotuned one")
-    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256w", "cta256s", "cta1024",
-                                                    "cta256x8"],
+    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256w", "cta256s", "cta512",
+                                                    "cta1024", "cta256x8"],
                     help="tiled forms with this tile shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")

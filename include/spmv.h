@@ -79,9 +79,16 @@ enum {
                                     default is one CTA per tile, with tiles
                                     sized so that they fill about one wave of
                                     resident CTAs */
-    SPMV_FLAG_STAGE = 16         /* stage x in 256-thread CTAs too; by default
-                                    only wide (1024-thread) CTAs stage, where
-                                    the window is large enough to pay */
+    SPMV_FLAG_STAGE = 16,        /* stage x in 256-thread CTAs too; by default
+                                    only 512- and 1024-thread CTAs stage, whose
+                                    windows are large enough to pay */
+    SPMV_FLAG_TEST_WAIT_EXPIRES = 32  /* tests of failure detection only: the
+                                    first wait of every staged tile on its
+                                    staging copy gives up at once, so every
+                                    staged tile is skipped and spmv_plan_check
+                                    reports SPMV_E_TIMEOUT (the copy is still
+                                    awaited, with the normal bound, before the
+                                    CTA exits) */
 };
 
 /* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,
@@ -139,9 +146,11 @@ typedef struct spmv_opts {
                              of 32 rows (0 = 64) */
     int32_t cta_threads;  /* tiled forms: 256 = several CTAs per SM, tiles
                              for one wave of them, x through L1/L2 (0 = this);
+                             512 = two CTAs per SM, tiles for two waves, each
+                             staging up to 96 KB of x in shared memory;
                              1024 = one wide CTA per SM, tiles for four waves,
-                             each staging up to 200 KB of x in shared memory
-                             (for parts with large column windows) */
+                             each staging up to 200 KB (for parts with large
+                             column windows) */
     /* optional device allocator for plan-owned memory (NULL = cudaMalloc) */
     void *(*alloc)(size_t bytes, void *ctx);
     void (*release)(void *ptr, void *ctx);
@@ -450,9 +459,12 @@ spmv_status spmv_csr_exec_noalloc(int32_t m, int32_t n, int64_t nnz,
  * SPMV_E_INTERNAL with the offending indices in spmv_last_error().
  * stats (may be NULL) receives SPMV_EMULATE_STATS counts: tiles, chunk
  * tiles, staged tiles, partial slots, fix-ups, warp rows, stored chunk
- * elements (with padding), 1 if the plain CSR kernel is used.  Errors: those
- * of spmv_plan_create's validation, SPMV_E_INTERNAL, SPMV_E_NOMEM. */
-#define SPMV_EMULATE_STATS 8
+ * elements (with padding), 1 if the plain CSR kernel is used, nonzeros whose
+ * x is gathered (not staged), FMA lanes the tiles issue, element slots that
+ * load x from both global and shared memory, x entries staged, tiles that
+ * stage a second run.  Errors: those of spmv_plan_create's validation,
+ * SPMV_E_INTERNAL, SPMV_E_NOMEM. */
+#define SPMV_EMULATE_STATS 13
 spmv_status spmv_plan_emulate(const spmv_csr *A, const spmv_perm *perm,
                               const spmv_splits *splits, const spmv_opts *opts,
                               int32_t n_sm, const double *x, double *y, int64_t *stats);

@@ -35,6 +35,7 @@ SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
 SPMV_NATURAL, SPMV_SB, SPMV_DB, SPMV_SPLIT = 0, 1, 2, 3
 SPMV_FLAG_NO_STAGING, SPMV_FLAG_TILED_NATURAL, SPMV_FLAG_SM_AFFINE = 1, 2, 4
 SPMV_FLAG_PERSISTENT, SPMV_FLAG_STAGE = 8, 16
+SPMV_FLAG_TEST_WAIT_EXPIRES = 32
 SPMV_PART_CN, SPMV_PART_ERCN, SPMV_PART_RCN, SPMV_PART_RANDOM = 0, 1, 2, 3
 SPMV_FIT_CSR, SPMV_FIT_X = 0, 1
 
@@ -51,9 +52,10 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched", "spmv_features",
            "spmv_mlp_param_count", "spmv_mlp_work_bytes", "spmv_mlp_forward", "spmv_mlp_grad",
            "spmv_mlp_adam", "spmv_plan_emulate")
-SPMV_EMULATE_STATS = 8
+SPMV_EMULATE_STATS = 13
 EMULATE_STATS = ("tiles", "chunk_tiles", "staged_tiles", "partial_slots", "fixups", "warp_rows",
-                 "stored_chunk_elements", "plain_csr")
+                 "stored_chunk_elements", "plain_csr", "gathered_nnz", "fma_lanes",
+                 "mixed_slots", "staged_entries", "two_run_tiles")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 

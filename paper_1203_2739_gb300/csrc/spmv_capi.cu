@@ -223,6 +223,7 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         if (tiled) {
             add_vec(a, hp.tiles, (const void **)&dp.tiles);
             add_vec(a, hp.chunk_off, (const void **)&dp.chunk_off);
+            add_vec(a, hp.chunk_mix, (const void **)&dp.chunk_mix);
             add_vec(a, hp.slot_dst, (const void **)&dp.slot_dst);
             add_vec(a, hp.slot_len, (const void **)&dp.slot_len);
             if (!hp.vrows.empty()) add_vec(a, hp.vrows, (const void **)&dp.vrows);
@@ -283,6 +284,7 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         dp.smem_bytes = any_staged ? (hp.max_staged * r * xb + 15) / 16 * 16 : 0;
         dp.nq = nq;
         dp.cta_threads = hp.cta_threads;
+        dp.wait_limit = (hp.flags & SPMV_FLAG_TEST_WAIT_EXPIRES) ? 0u : (1u << 22);
         if (tiled) {
             e = cudaDeviceGetAttribute(&dp.n_sm, cudaDevAttrMultiProcessorCount, p->device);
             if (e != cudaSuccess) {
@@ -360,9 +362,10 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
                     }
             }
             I.moved_bytes = hp.nnz * vb + hp.narrow_nnz * 2 + (hp.nnz - hp.narrow_nnz) * 4 +
-                            (int64_t)hp.slot_dst.size() * 8 + (int64_t)hp.chunk_off.size() * 4 +
+                            (int64_t)hp.slot_dst.size() * 8 + (int64_t)hp.chunk_off.size() * 8 +
                             (int64_t)hp.vrows.size() * 16 +
-                            (int64_t)hp.tiles.size() * 48 + hp.staged_entries * r * xb +
+                            (int64_t)hp.tiles.size() * (int64_t)sizeof(Tile) +
+                            hp.staged_entries * r * xb +
                             hp.list_entries * 4 + gdistinct * r * xb + (int64_t)hp.m * r * xb +
                             hp.partial_slots * r * xb * 2 + (int64_t)hp.fixups.size() * 16;
         }

@@ -20,6 +20,7 @@ struct DevPlan {
     const Tile *tiles = nullptr;
     int32_t n_tiles = 0;
     const int32_t *chunk_off = nullptr;
+    const int32_t *chunk_mix = nullptr;
     const int32_t *slot_dst = nullptr;
     const int32_t *slot_len = nullptr;
     const VRow *vrows = nullptr;
@@ -33,10 +34,11 @@ struct DevPlan {
     int32_t *qcount = nullptr;         // nq + 1 counters, zero between launches
     int32_t nq = 0;
     int32_t *status = nullptr;         // 1 after a bounded device wait gave up
+    uint32_t wait_limit = 1u << 22;    // polls of the first wait on a staging copy
     // persistent schedule (ctr = NULL: one CTA per tile)
     int32_t *ctr = nullptr;            // next-tile counter, finished-CTA counter
     int32_t n_sm = 0;
-    int32_t cta_threads = 256;         // 256, or 1024 (wide: one CTA per SM)
+    int32_t cta_threads = 256;         // 256, 512 (two per SM) or 1024 (one per SM)
 };
 
 cudaError_t exec_f64(const DevPlan &P, const void *x, void *y, cudaStream_t s);

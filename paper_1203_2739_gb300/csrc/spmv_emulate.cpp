@@ -128,20 +128,27 @@ bool run_tile(Emu &E, const Tile &t)
     }
     if (t.kind != TILE_NARROW && t.kind != TILE_MIXED && t.kind != TILE_GLOBAL)
         return E.fail("tile kind", t.kind, 0);
-    // the staged window: the contiguous run, then the gathered list
-    E.n_win = t.runlen + t.listlen;
-    if (t.runlen < 0 || t.listlen < 0) return E.fail("window lengths", t.runlen, t.listlen);
+    // the staged window: the first run, the second run (at run2_at), then
+    // the gathered list
+    if (t.runlen < 0 || t.run2len < 0 || t.listlen < 0)
+        return E.fail("window lengths", t.runlen, t.listlen);
+    if (t.run2_at < t.runlen) return E.fail("second run overlaps the first", t.run2_at, t.runlen);
+    E.n_win = t.run2_at + t.run2len + t.listlen;
     if (t.kind == TILE_NARROW && E.n_win > 65536) return E.fail("narrow window", E.n_win, 0);
     // the device's preconditions: the window fits the dynamic shared memory
-    // the launch reserves (max_staged entries), and the bulk copy of the
-    // run's 16-byte body starts on a 16-byte boundary of x_hat
+    // the launch reserves (max_staged entries); each run's bulk copy starts
+    // on a 16-byte boundary of x_hat and of shared memory
     if (E.n_win > P.max_staged) return E.fail("window beyond the reserved shared memory",
                                               E.n_win, P.max_staged);
     {
         const int64_t xb = P.dtype == SPMV_F64 ? 8 : 4;
-        const int64_t body = ((int64_t)t.runlen * r * xb) & ~(int64_t)15;
-        if (body > 0 && ((int64_t)t.run0 * r * xb) % 16 != 0)
+        const int64_t body1 = ((int64_t)t.runlen * r * xb) & ~(int64_t)15;
+        const int64_t body2 = ((int64_t)t.run2len * r * xb) & ~(int64_t)15;
+        if (body1 > 0 && ((int64_t)t.run0 * r * xb) % 16 != 0)
             return E.fail("bulk copy source not 16-byte aligned", t.run0, r);
+        if (body2 > 0 && (((int64_t)t.run2_0 * r * xb) % 16 != 0 ||
+                          ((int64_t)t.run2_at * r * xb) % 16 != 0))
+            return E.fail("second bulk copy not 16-byte aligned", t.run2_0, t.run2_at);
         if ((int64_t)P.max_staged * r * xb > 227 * 1024)
             return E.fail("reserved shared memory beyond 227 KB", P.max_staged, r);
     }
@@ -151,13 +158,20 @@ bool run_tile(Emu &E, const Tile &t)
         if (g < 0 || g >= P.n) return E.fail("staged run", g, P.n);
         for (int32_t k = 0; k < r; ++k) E.win[(size_t)i * r + k] = E.xh[(size_t)g * r + k];
     }
+    for (int32_t i = 0; i < t.run2len; ++i) {
+        const int64_t g = (int64_t)t.run2_0 + i;
+        if (g < 0 || g >= P.n) return E.fail("second staged run", g, P.n);
+        for (int32_t k = 0; k < r; ++k)
+            E.win[(size_t)(t.run2_at + i) * r + k] = E.xh[(size_t)g * r + k];
+    }
+    const int32_t lat = t.run2_at + t.run2len;
     for (int32_t i = 0; i < t.listlen; ++i) {
         const int64_t q = (int64_t)t.list0 + i;
         if (q < 0 || q >= (int64_t)P.xlist.size()) return E.fail("staging list", q, 0);
         const int32_t g = P.xlist[(size_t)q];
         if (g < 0 || g >= P.n) return E.fail("staged list entry", g, P.n);
         for (int32_t k = 0; k < r; ++k)
-            E.win[(size_t)(t.runlen + i) * r + k] = E.xh[(size_t)g * r + k];
+            E.win[(size_t)(lat + i) * r + k] = E.xh[(size_t)g * r + k];
     }
     if (t.kind == TILE_GLOBAL && E.n_win != 0) return E.fail("global tile stages", E.n_win, 0);
     // rows reduced by a warp
@@ -182,6 +196,20 @@ bool run_tile(Emu &E, const Tile &t)
         // the kernel reads every lane up to the longest row (padding included)
         if (off < 0 || off + 32 * (int64_t)longest > (int64_t)P.val.size())
             return E.fail("chunk storage", ch, off);
+        if (ch >= (int64_t)P.chunk_mix.size()) return E.fail("chunk mix prefix", ch, 0);
+        const int32_t G = P.chunk_mix[(size_t)ch];
+        if (G < 0 || G > longest || (t.kind != TILE_MIXED && G != 0))
+            return E.fail("chunk mix prefix", ch, G);
+        if (t.kind == TILE_MIXED) {
+            // from slot G on the kernel reads shared memory only: every
+            // stored element there (padding included) must be a staged index
+            for (int64_t k = G; k < longest; ++k)
+                for (int32_t i = 0; i < 32; ++i) {
+                    const int32_t c = P.col32[(size_t)(off + 32 * k + i)];
+                    if (c < 0 || c >= E.n_win)
+                        return E.fail("element past the mix prefix is not staged", ch, k);
+                }
+        }
         for (int32_t i = 0; i < 32; ++i) {
             const int32_t len = P.slot_len[(size_t)ch * 32 + i];
             const int32_t dst = P.slot_dst[(size_t)ch * 32 + i];
@@ -259,10 +287,15 @@ extern "C" spmv_status spmv_plan_emulate(const spmv_csr *A, const spmv_perm *per
         }
         if (stats) {
             int32_t nvr = 0;
-            for (const Tile &t : P.tiles) nvr += t.kind == TILE_CHUNK ? 0 : t.nvrows;
+            int64_t two_runs = 0;
+            for (const Tile &t : P.tiles) {
+                nvr += t.kind == TILE_CHUNK ? 0 : t.nvrows;
+                two_runs += t.kind != TILE_CHUNK && t.run2len > 0;
+            }
             const int64_t v[SPMV_EMULATE_STATS] = {
                 (int64_t)P.tiles.size(), P.n_chunk_tiles, P.n_staged_tiles, P.partial_slots,
-                (int64_t)P.fixups.size(), nvr, P.padded_elems, P.use_k1 ? 1 : 0};
+                (int64_t)P.fixups.size(), nvr, P.padded_elems, P.use_k1 ? 1 : 0,
+                P.direct_nnz, P.fma_slots, P.mixed_slots, P.staged_entries, two_runs};
             for (int k = 0; k < SPMV_EMULATE_STATS; ++k) stats[k] = v[k];
         }
         return SPMV_OK;

@@ -35,16 +35,27 @@ enum TileKind : int32_t {
     TILE_CHUNK = 3     // elements [e0, e1) of one long row -> partial slot
 };
 
-struct Tile {          // 48 bytes, copied to the device as is
+// The staged window of a tile is up to two contiguous runs of x_hat and a
+// gathered list, back to back in shared memory:
+//   smem[0 .. runlen)                   = x_hat[run0 .. run0 + runlen)
+//   smem[run2_at .. run2_at + run2len)  = x_hat[run2_0 .. run2_0 + run2len)
+//   smem[run2_at + run2len + i]         = x_hat[xlist[list0 + i]]
+// Each run starts on a 16-byte boundary of x_hat and of shared memory (its
+// bulk copy needs both); run2_at rounds the first run's length up to that.
+struct Tile {          // 64 bytes, copied to the device as is
     int32_t kind;
     int32_t chunk0, nchunks;  // chunks of 32 rows (not CHUNK tiles)
     int32_t slot;             // CHUNK: the partial slot it writes
-    int32_t run0, runlen;     // x_hat[run0 + i] -> smem[i]
-    int32_t list0, listlen;   // x_hat[xlist[list0 + i]] -> smem[runlen + i]
+    int32_t run0, runlen;     // first staged run
+    int32_t run2_0, run2len;  // second staged run
+    int32_t list0, listlen;   // gathered list
     int32_t e0, e1;           // CHUNK: element range (contiguous, global indices)
     int32_t vrow0, nvrows;    // rows too long for one lane: vrows[vrow0 ..]
+    int32_t run2_at;          // shared-memory entry where the second run starts
+                              // (the first run's length rounded up to 16 bytes)
+    int32_t pad;
 };
-static_assert(sizeof(Tile) == 48, "Tile layout");
+static_assert(sizeof(Tile) == 64, "Tile layout");
 
 // A row of a tile reduced by a whole warp: elements [e0, e0 + len) stored
 // contiguously with the tile's index encoding; dst as slot_dst.
@@ -80,6 +91,11 @@ struct HostPlan {
 
     std::vector<Tile> tiles;
     std::vector<int32_t> chunk_off;  // element offset of each chunk
+    // MIXED tiles: per chunk, the number of leading element slots that may
+    // read x from global memory; every lane's elements from that slot on
+    // are staged (each row stores its gathered elements first).  Other
+    // tiles: 0.
+    std::vector<int32_t> chunk_mix;
     std::vector<int32_t> slot_dst;   // 32 per chunk
     std::vector<int32_t> slot_len;   // 32 per chunk (row length, 0 if empty)
     std::vector<VRow> vrows;
@@ -90,7 +106,10 @@ struct HostPlan {
     int64_t staged_entries = 0, list_entries = 0, direct_nnz = 0, narrow_nnz = 0;
     int32_t max_staged = 0;        // most x entries one tile stages
     int64_t padded_elems = 0;      // stored elements (with padding) in chunks
-    int64_t fma_slots = 0;         // sum over chunks of 32 * (longest row)
+    int64_t fma_slots = 0;         // FMA lanes issued: 32 * (longest row) per chunk,
+                                   // 32 * ceil(len / 32) per warp row
+    int64_t mixed_slots = 0;       // element slots of MIXED chunks that load x
+                                   // from both global and shared memory
 
     std::vector<int32_t> row_perm, col_perm;  // empty = identity
 };

@@ -43,6 +43,7 @@
 namespace spmv {
 
 constexpr int kThreads = 256;
+constexpr int kMidThreads = 512;
 constexpr int kWideThreads = 1024;
 
 // Tuning knobs (compile-time):
@@ -177,20 +178,26 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
-                                              uint64_t *bar)
+// One arrival that expects `bytes` of asynchronous copies on the barrier.
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes)
 {
     // order earlier generic-proxy reads of the destination (a previous tile)
     // before the async-proxy writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// A bulk copy global -> shared memory completing on the barrier (both
+// addresses 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
+// Poll the barrier's phase at most `limit` times.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, uint32_t limit)
 {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -297,7 +304,7 @@ k_csr_vector(const int32_t m, const int32_t *__restrict__ rowptr, const int32_t 
 template <typename VT, typename XT>
 struct TileArgs {
     const Tile *tiles;
-    const int32_t *chunk_off, *slot_dst, *slot_len;
+    const int32_t *chunk_off, *chunk_mix, *slot_dst, *slot_len;
     const VRow *vrows;
     const uint16_t *c16;
     const int32_t *c32;
@@ -310,24 +317,26 @@ struct TileArgs {
     int32_t *qcount;        // nq claim counters, then one finished-CTA counter
     int32_t nq;
     int32_t *status;        // set to 1 when a bounded wait gives up
+    uint32_t wait_limit;    // polls of the first wait on a tile's staging copy
 };
 
-// One tile.  After staging, warp w takes chunks w, w+8, ...; lane i owns row
-// i of the chunk and runs one FMA chain over its row: element k of the
-// chunk's rows sits at chunk_off + 32 k + i, so every load is coalesced and
-// every FP64 FMA runs with the lanes of all rows still going.
-// The x entries of one stored element for all right-hand sides.  NARROW:
-// staged; GLOBAL: gathered from L2; MIXED (ci < 0: gathered entry ~ci):
-// both loads are issued -- the unused one reads entry 0 -- and one is
-// selected, so the gathers of a batch carry no branch and are all in flight
-// together.
-template <int KIND, int R, typename XT>
+// How one stored element finds its x entries.
+enum : int {
+    FX_GLOBAL = 0,   // col32 is an x_hat index: gathered through L1 / L2
+    FX_MIXED = 1,    // col32 >= 0: staged entry; col32 < 0: x_hat[~col32].  Both
+                     // loads are issued (the unused one reads entry 0) and one
+                     // is selected, so a batch has no branch
+    FX_SMEM32 = 2,   // col32 is a staged entry
+    FX_SMEM16 = 3    // col16 is a staged entry (narrow tiles)
+};
+
+template <int FX, int R, typename XT>
 __device__ __forceinline__ void fetch_x(int32_t ci, const XT *seg, const XT *__restrict__ x,
                                         XT (&o)[R])
 {
-    if (KIND == TILE_NARROW) {
+    if constexpr (FX == FX_SMEM16 || FX == FX_SMEM32) {
         load_xrow<R, XT, false>(seg + ci * R, o);
-    } else if (KIND == TILE_GLOBAL) {
+    } else if constexpr (FX == FX_GLOBAL) {
         load_xrow<R, XT, true>(x + (int64_t)ci * R, o);
     } else {
         const bool g = ci < 0;
@@ -341,15 +350,128 @@ __device__ __forceinline__ void fetch_x(int32_t ci, const XT *seg, const XT *__r
     }
 }
 
-// The rows of a tile after staging, for one tile kind.  Loads are issued for
-// every slot of a batch (slots past a row's end read element 0 of the
-// chunk, a valid address) and the FMAs of those slots are discarded by a
-// select, so a batch has no branches.
+template <int FX>
+__device__ __forceinline__ int32_t load_col(const int32_t *__restrict__ c32,
+                                            const uint16_t *__restrict__ c16, int64_t e)
+{
+    if constexpr (FX == FX_SMEM16) return (int32_t)ld_stream(c16 + e);
+    else return ld_stream(c32 + e);
+}
+
+// Element slots [k0, k0 + UB) of a chunk (k0 + UB <= the chunk's longest
+// row, so every slot exists for the warp): element k of lane i is at
+// off + 32 k + i.  All UB value / index loads are issued before the UB
+// gathers, and all gathers before the FMAs, so UB gathers per lane are in
+// flight together.  Lanes whose row ended keep their sum (a select, no
+// branch); padding slots hold index 0, a valid entry.
+template <int FX, int UB, int R, typename VT, typename XT>
+__device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len,
+                                            const VT *__restrict__ val,
+                                            const int32_t *__restrict__ c32,
+                                            const uint16_t *__restrict__ c16, const XT *seg,
+                                            const XT *__restrict__ x, XT (&s)[R])
+{
+    XT v[UB];
+    int32_t ci[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        const int64_t e = off + (int64_t)(k0 + u) * 32;
+        v[u] = (XT)load_val(val + e);
+        ci[u] = load_col<FX>(c32, c16, e);
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        XT xo[R];
+        fetch_x<FX, R, XT>(ci[u], seg, x, xo);
+        const bool on = k0 + u < len;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            const XT f = fma(v[u], xo[c], s[c]);
+            s[c] = on ? f : s[c];
+        }
+    }
+}
+
+// Slots [kb, ke) of a chunk: full batches of U, then the remainder in
+// batches of 4, 2 and 1 (ke is the same for the whole warp, so these
+// branches do not diverge).  Exactly ke - kb FMAs per lane are issued: on
+// GB300, which runs two FP64 FMAs per SM per clock, a padded batch would
+// cost as much as a useful one.
+template <int FX, int U, int R, typename VT, typename XT>
+__device__ __forceinline__ void chunk_span(int32_t kb, int32_t ke, int64_t off, int32_t len,
+                                           const VT *__restrict__ val,
+                                           const int32_t *__restrict__ c32,
+                                           const uint16_t *__restrict__ c16, const XT *seg,
+                                           const XT *__restrict__ x, XT (&s)[R])
+{
+    int32_t k0 = kb;
+    for (; k0 + U <= ke; k0 += U) chunk_batch<FX, U, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+    if constexpr (U > 4) {
+        if ((ke - k0) & 4) {
+            chunk_batch<FX, 4, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+            k0 += 4;
+        }
+    }
+    if constexpr (U > 2) {
+        if ((ke - k0) & 2) {
+            chunk_batch<FX, 2, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+            k0 += 2;
+        }
+    }
+    if constexpr (U > 1) {
+        if ((ke - k0) & 1) chunk_batch<FX, 1, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+    }
+}
+
+// A row reduced by a whole warp: batches of U elements per lane (slots past
+// the row's end read the row's first element and are discarded), then a
+// shuffle sum.
+template <int FX, int U, int R, typename VT, typename XT>
+__device__ __forceinline__ void warp_row(const VRow &row, const VT *__restrict__ val,
+                                         const int32_t *__restrict__ c32,
+                                         const uint16_t *__restrict__ c16, const XT *seg,
+                                         const XT *__restrict__ x, XT (&s)[R])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < R; ++c) s[c] = XT(0);
+    for (int32_t k0 = 0; k0 < row.len; k0 += 32 * U) {
+        XT v[U];
+        int32_t ci[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t k = k0 + u * 32 + lane;
+            const int64_t e = row.e0 + (k < row.len ? k : 0);
+            v[u] = (XT)load_val(val + e);
+            ci[u] = load_col<FX>(c32, c16, e);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            XT xo[R];
+            fetch_x<FX, R, XT>(ci[u], seg, x, xo);
+            const bool on = k0 + u * 32 + lane < row.len;
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+                const XT f = fma(v[u], xo[c], s[c]);
+                s[c] = on ? f : s[c];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < R; ++c) s[c] = group_sum<32>(s[c]);
+}
+
+// The rows of a tile after staging.  Warp w takes the warp rows w, w + NT/32,
+// ..., then the chunks w, w + NT/32, ...: lane i owns row i of a chunk and
+// runs one FMA chain over it.  A chunk's metadata (row lengths,
+// destinations, offset, mixed prefix) is loaded one chunk ahead, so a chunk
+// costs two dependent trips to memory (its stream, then its gathers).
 template <int KIND, int R, typename VT, typename XT, int NT>
 __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> &A,
                                           const XT *seg)
 {
     const int32_t *__restrict__ chunk_off = A.chunk_off;
+    const int32_t *__restrict__ chunk_mix = A.chunk_mix;
     const int32_t *__restrict__ slot_dst = A.slot_dst;
     const int32_t *__restrict__ slot_len = A.slot_len;
     const VRow *__restrict__ vrows = A.vrows;
@@ -360,9 +482,6 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
     XT *__restrict__ y = A.y;
     XT *__restrict__ partial = A.partial;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    auto colat = [&](int64_t e) -> int32_t {
-        return KIND == TILE_NARROW ? (int32_t)ld_stream(c16 + e) : ld_stream(c32 + e);
-    };
     auto store = [&](int32_t d, const XT (&s)[R]) {
         if (d >= 0) {
 #pragma unroll
@@ -373,90 +492,50 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
             for (int c = 0; c < R; ++c) partial[ps + c] = s[c];
         }
     };
-    // elements per lane in flight per batch (the wide CTAs have the larger
+    // elements per lane in flight per batch (the wider CTAs have the larger
     // register budget)
     constexpr int U = (R == 1 ? (NT == kThreads ? 8 : SPMV_WIDE_U) : (R == 2 ? 4 : 2));
+    constexpr int FXW = KIND == TILE_NARROW ? FX_SMEM16 : (KIND == TILE_MIXED ? FX_MIXED : FX_GLOBAL);
 
-    // rows too long for one lane: a warp each, batches of U loads per lane
     for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += NT / 32) {
         const VRow row = vrows[vr];
         XT s[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = XT(0);
-        for (int32_t k0 = 0; k0 < row.len; k0 += 32 * U) {
-            XT v[U];
-            int32_t ci[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int32_t k = k0 + u * 32 + lane;
-                const int64_t e = row.e0 + (k < row.len ? k : 0);
-                v[u] = (XT)load_val(val + e);
-                ci[u] = colat(e);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                XT xo[R];
-                fetch_x<KIND, R, XT>(ci[u], seg, x, xo);
-                const bool on = k0 + u * 32 + lane < row.len;
-#pragma unroll
-                for (int c = 0; c < R; ++c) {
-                    const XT f = fma(v[u], xo[c], s[c]);
-                    s[c] = on ? f : s[c];
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = group_sum<32>(s[c]);
+        warp_row<FXW, U, R, VT, XT>(row, val, c32, c16, seg, x, s);
         if (lane == 0) store(row.dst, s);
     }
 
-    // chunks of 32 rows, one lane per row, batches of U elements per lane.
-    // A chunk's metadata (row length, destination, offset) is loaded one
-    // chunk ahead, so a chunk costs two dependent trips to memory (its
-    // stream, then its gathers) instead of four.
     const int32_t cend = t.chunk0 + t.nchunks;
     int32_t ch = t.chunk0 + warp;
-    int32_t len_n = 0, dst_n = -1, off_n = 0;
+    int32_t len_n = 0, dst_n = -1, off_n = 0, mix_n = 0;
     if (ch < cend) {
         len_n = __ldg(slot_len + ch * 32 + lane);
         dst_n = __ldg(slot_dst + ch * 32 + lane);
         off_n = __ldg(chunk_off + ch);
+        if (KIND == TILE_MIXED) mix_n = __ldg(chunk_mix + ch);
     }
     for (; ch < cend; ch += NT / 32) {
-        const int32_t len = len_n, dst = dst_n;
+        const int32_t len = len_n, dst = dst_n, G = mix_n;
         const int64_t off = (int64_t)off_n + lane;
         const int32_t chn = ch + NT / 32;
         if (chn < cend) {
             len_n = __ldg(slot_len + chn * 32 + lane);
             dst_n = __ldg(slot_dst + chn * 32 + lane);
             off_n = __ldg(chunk_off + chn);
+            if (KIND == TILE_MIXED) mix_n = __ldg(chunk_mix + chn);
         }
         const int32_t L = __shfl_sync(0xffffffffu, len, 0);   // rows sorted: lane 0 is longest
         XT s[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) s[c] = XT(0);
-        for (int32_t k0 = 0; k0 < L; k0 += U) {
-            XT v[U];
-            int32_t ci[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                // slots past the row's end (or past the chunk's longest row)
-                // read the chunk's first element
-                const int64_t e = off + (k0 + u < L ? (int64_t)(k0 + u) * 32 : 0);
-                v[u] = (XT)load_val(val + e);
-                ci[u] = colat(e);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                XT xo[R];
-                fetch_x<KIND, R, XT>(ci[u], seg, x, xo);
-                const bool on = k0 + u < len;
-#pragma unroll
-                for (int c = 0; c < R; ++c) {
-                    const XT f = fma(v[u], xo[c], s[c]);
-                    s[c] = on ? f : s[c];
-                }
-            }
+        if constexpr (KIND == TILE_MIXED) {
+            // rows store their gathered elements first: slots [0, G) may
+            // gather, slots [G, L) read shared memory only
+            chunk_span<FX_MIXED, U, R, VT, XT>(0, G, off, len, val, c32, c16, seg, x, s);
+            chunk_span<FX_SMEM32, U, R, VT, XT>(G, L, off, len, val, c32, c16, seg, x, s);
+        } else if constexpr (KIND == TILE_NARROW) {
+            chunk_span<FX_SMEM16, U, R, VT, XT>(0, L, off, len, val, c32, c16, seg, x, s);
+        } else {
+            chunk_span<FX_GLOBAL, U, R, VT, XT>(0, L, off, len, val, c32, c16, seg, x, s);
         }
         store(dst, s);
     }
@@ -471,16 +550,10 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     XT *seg = reinterpret_cast<XT *>(smem_raw);
-    const int32_t *__restrict__ chunk_off = A.chunk_off;
-    const int32_t *__restrict__ slot_dst = A.slot_dst;
-    const int32_t *__restrict__ slot_len = A.slot_len;
-    const VRow *__restrict__ vrows = A.vrows;
-    const uint16_t *__restrict__ c16 = A.c16;
-    const int32_t *__restrict__ c32 = A.c32;
     const VT *__restrict__ val = A.val;
+    const int32_t *__restrict__ c32 = A.c32;
     const int32_t *__restrict__ xlist = A.xlist;
     const XT *__restrict__ x = A.x;
-    XT *__restrict__ y = A.y;
     XT *__restrict__ partial = A.partial;
 
     if (t.kind == TILE_CHUNK) {
@@ -505,17 +578,25 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
 
     const int kind = t.kind;
     if (kind != TILE_GLOBAL) {
-        // stage the reused x entries: the contiguous run (one bulk copy of
-        // its 16-byte-aligned body; the plan aligns the run's start and its
-        // end unless it ends at x's end), then the gathered list
-        const int32_t run_elems = t.runlen * R;
-        const uint32_t body = (uint32_t)(run_elems * (int32_t)sizeof(XT)) & ~15u;
-        if (threadIdx.x == 0 && body > 0)
-            bulk_copy_g2s(seg, x + (int64_t)t.run0 * R, body, bar);
-        for (int32_t i = (int32_t)(body / sizeof(XT)) + threadIdx.x; i < run_elems; i += NT)
+        // stage the window: the 16-byte bodies of the two runs by bulk copy
+        // (one elected thread, one mbarrier for both), their tails and the
+        // gathered list by the CTA's threads
+        const int32_t n1 = t.runlen * R, n2 = t.run2len * R, at2 = t.run2_at * R;
+        const uint32_t body1 = (uint32_t)(n1 * (int32_t)sizeof(XT)) & ~15u;
+        const uint32_t body2 = (uint32_t)(n2 * (int32_t)sizeof(XT)) & ~15u;
+        const bool copy = body1 + body2 > 0;
+        if (threadIdx.x == 0 && copy) {
+            mbar_expect(bar, body1 + body2);
+            if (body1) bulk_g2s(seg, x + (int64_t)t.run0 * R, body1, bar);
+            if (body2) bulk_g2s(seg + at2, x + (int64_t)t.run2_0 * R, body2, bar);
+        }
+        for (int32_t i = (int32_t)(body1 / sizeof(XT)) + threadIdx.x; i < n1; i += NT)
             seg[i] = __ldg(x + (int64_t)t.run0 * R + i);
-        // list: batches of 8 entries per thread, every index load issued
+        for (int32_t i = (int32_t)(body2 / sizeof(XT)) + threadIdx.x; i < n2; i += NT)
+            seg[at2 + i] = __ldg(x + (int64_t)t.run2_0 * R + i);
+        // list: batches of entries per thread, every index load issued
         // before the gathers that depend on them
+        const int32_t lat = at2 + n2;
         constexpr int LB = R == 1 ? 8 : (R == 2 ? 4 : (R == 4 ? 2 : 1));
         for (int32_t i0 = 0; i0 < t.listlen; i0 += LB * NT) {
             int32_t src[LB];
@@ -535,20 +616,20 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
                 const int32_t i = i0 + u * NT + (int32_t)threadIdx.x;
                 if (i < t.listlen) {
 #pragma unroll
-                    for (int c = 0; c < R; ++c) seg[(t.runlen + i) * R + c] = v[u][c];
+                    for (int c = 0; c < R; ++c) seg[lat + i * R + c] = v[u][c];
                 }
             }
         }
         bool ok = true;
-        if (body > 0) ok = mbar_wait(bar, phase);
+        if (copy) ok = mbar_wait(bar, phase, A.wait_limit);
         ok = __syncthreads_and(ok);
-        if (body > 0) phase ^= 1u;
+        if (copy) phase ^= 1u;
         if (!ok) {
             // the copy is still owed to this barrier: wait once more (bounded)
             // before the CTA leaves, then report
             if (threadIdx.x == 0) {
                 atomicExch(A.status, 1);
-                mbar_wait(bar, phase ^ 1u);
+                mbar_wait(bar, phase ^ 1u, kWaitLimit);
             }
             return false;
         }
@@ -563,9 +644,12 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
 }
 
 // One CTA per tile, in tile order.  NT = kThreads: several CTAs per SM;
-// NT = kWideThreads: one wide CTA per SM with a large staging window.
+// NT = kMidThreads: two CTAs per SM, each with about half of the SM's shared
+// memory for its window; NT = kWideThreads: one wide CTA per SM with a large
+// staging window.
 template <int R, typename VT, typename XT, int NT>
-__global__ void __launch_bounds__(NT, NT == kThreads ? tile_ctas_per_sm(R) : 1)
+__global__ void __launch_bounds__(NT, NT == kThreads ? tile_ctas_per_sm(R)
+                                                     : (NT == kMidThreads ? 2 : 1))
 k_tiles(const TileArgs<VT, XT> A)
 {
     __shared__ __align__(8) uint64_t bar;
@@ -810,6 +894,7 @@ cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
         TileArgs<VT, XT> A;
         A.tiles = P.tiles;
         A.chunk_off = P.chunk_off;
+        A.chunk_mix = P.chunk_mix;
         A.slot_dst = P.slot_dst;
         A.slot_len = P.slot_len;
         A.vrows = P.vrows;
@@ -824,6 +909,7 @@ cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
         A.qcount = P.qcount;
         A.nq = P.nq;
         A.status = P.status;
+        A.wait_limit = P.wait_limit;
         cudaError_t e;
         if (P.nq > 0) {
             auto kern = k_tiles_affine<R, VT, XT>;
@@ -850,6 +936,11 @@ cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
             e = ensure_smem(kern, P.smem_bytes);
             if (e != cudaSuccess) return e;
             kern<<<(unsigned)P.n_tiles, kWideThreads, P.smem_bytes, s>>>(A);
+        } else if (P.cta_threads == kMidThreads) {
+            auto kern = k_tiles<R, VT, XT, kMidThreads>;
+            e = ensure_smem(kern, P.smem_bytes);
+            if (e != cudaSuccess) return e;
+            kern<<<(unsigned)P.n_tiles, kMidThreads, P.smem_bytes, s>>>(A);
         } else {
             auto kern = k_tiles<R, VT, XT, kThreads>;
             e = ensure_smem(kern, P.smem_bytes);

@@ -247,7 +247,7 @@ struct Tiler {
         : cfg(c), prp(rp), col(cl), pval(pv), pdst(pd), P(plan), mark((size_t)n, -1),
           cnt((size_t)n, 0), loc((size_t)n, 0) {}
 
-    // the aligned run covering home columns [lo, hi]
+    // the aligned run covering columns [lo, hi]
     void aligned_run(int32_t lo, int32_t hi, int32_t *run0, int32_t *runlen) const
     {
         const int32_t a = cfg.align;
@@ -256,6 +256,98 @@ struct Tiler {
         e = std::min<int64_t>(cfg.n, (e + a - 1) / a * a);
         *run0 = b;
         *runlen = (int32_t)(e - b);
+    }
+
+    // The contiguous range of x_hat of at most `span` columns that maximises
+    // (uses covered) - lam * (columns spanned), over the tile's columns cs
+    // (ascending), skipping columns in [skip0, skip1): a staged entry costs
+    // lam of a gathered use (its bytes copied in bulk against the 32-byte
+    // sector a gather fetches).  Returns the uses covered (0 if no range
+    // scores above 0) and the first / last column.
+    int64_t best_window(const std::vector<int32_t> &cs, int32_t span, double lam,
+                        int32_t skip0, int32_t skip1, int32_t *lo, int32_t *hi) const
+    {
+        *lo = 0;
+        *hi = -1;
+        if (span <= 0 || cs.empty()) return 0;
+        // score(i..j) = P[j+1] - P[i] - lam (c_j - c_i + 1); for each j the
+        // best i within the span maximises lam c_i - P[i] (a monotone deque)
+        const size_t n = cs.size();
+        std::vector<double> P(n + 1, 0.0);
+        for (size_t j = 0; j < n; ++j) P[j + 1] = P[j] + cnt[cs[j]];
+        std::vector<size_t> dq(n);
+        size_t qh = 0, qt = 0;
+        double best = 0.0;
+        int64_t best_uses = 0;
+        auto key = [&](size_t i) { return lam * cs[i] - P[i]; };
+        for (size_t j = 0; j < n; ++j) {
+            const int32_t c = cs[j];
+            if (c >= skip0 && c < skip1) {
+                qh = qt = 0;            // a range may not straddle the skipped one
+                continue;
+            }
+            while (qt > qh && key(dq[qt - 1]) <= key(j)) --qt;
+            dq[qt++] = j;
+            while ((int64_t)c - cs[dq[qh]] + 1 > span) ++qh;
+            const size_t i = dq[qh];
+            const double sc = P[j + 1] - P[i] - lam * ((double)c - cs[i] + 1);
+            if (sc > best) {
+                best = sc;
+                *lo = cs[i];
+                *hi = c;
+                best_uses = (int64_t)(P[j + 1] - P[i]);
+            }
+        }
+        return best_uses;
+    }
+
+    // A staging set: up to two runs and a list, the uses it covers (x
+    // gathers it saves) and its cost in gathers: a run entry costs its bytes
+    // over a 32-byte sector (what a gather of it would fetch), a list entry a
+    // gather.
+    struct Stage {
+        int32_t run0 = 0, runlen = 0, run2_0 = 0, run2len = 0, run2_at = 0;
+        std::vector<int32_t> list;
+        int64_t saved = 0;
+        double cost = 0.0;
+        double gain() const { return (double)saved - cost; }
+        int32_t entries() const { return run2_at + run2len + (int32_t)list.size(); }
+    };
+
+    double lam() const { return std::min(1.0, cfg.entry_bytes / 32.0); }
+
+    bool in_runs(const Stage &g, int32_t c) const
+    {
+        return (c >= g.run0 && c < g.run0 + g.runlen) ||
+               (c >= g.run2_0 && c < g.run2_0 + g.run2len);
+    }
+
+    // Complete a set whose runs are chosen: uses covered by the runs, then
+    // the most used of the other columns (list_min uses or more) on the list
+    // while capacity lasts.
+    void finish_stage(Stage &g, const std::vector<int32_t> &cs) const
+    {
+        std::vector<int32_t> rest;
+        g.saved = 0;
+        for (int32_t c : cs) {
+            if (in_runs(g, c)) g.saved += cnt[c];
+            else if (cnt[c] >= cfg.list_min) rest.push_back(c);
+        }
+        g.run2_at = g.run2len > 0 ? (g.runlen + cfg.align - 1) / cfg.align * cfg.align
+                                  : g.runlen;
+        const int64_t room = (int64_t)cfg.W - g.run2_at - g.run2len;
+        if ((int64_t)rest.size() > room) {
+            const size_t keep = (size_t)std::max<int64_t>(room, 0);
+            std::nth_element(rest.begin(), rest.begin() + keep, rest.end(),
+                             [&](int32_t x, int32_t y) {
+                                 return cnt[x] != cnt[y] ? cnt[x] > cnt[y] : x < y;
+                             });
+            rest.resize(keep);
+        }
+        std::sort(rest.begin(), rest.end());
+        for (int32_t c : rest) g.saved += cnt[c];
+        g.list.swap(rest);
+        g.cost = (double)(g.runlen + g.run2len) * lam() + (double)g.list.size();
     }
 
     // Close the tile made of plan rows `rows`; its columns carry mark == stamp
@@ -267,78 +359,87 @@ struct Tiler {
         Tile t{};
         t.kind = TILE_GLOBAL;
         if (cfg.stage && !force_global && tile_nnz > 0) {
-            auto home = [&](int32_t c) { return c >= h0 && c < h1; };
-            // option (a): the run over the used home columns + reused border
-            int32_t lo = INT32_MAX, hi = -1;
-            for (int32_t c : used)
-                if (home(c)) {
-                    lo = std::min(lo, c);
-                    hi = std::max(hi, c);
-                }
-            int32_t run0 = 0, runlen = 0;
-            if (hi >= 0) aligned_run(lo, hi, &run0, &runlen);
-            int64_t a_list = 0, a_saved = 0;
-            for (int32_t c : used) {
-                if (hi >= 0 && c >= run0 && c < run0 + runlen) a_saved += cnt[c];
-                else if (cnt[c] >= cfg.list_min) {
-                    ++a_list;
-                    a_saved += cnt[c];
+            std::vector<int32_t> cs(used);
+            std::sort(cs.begin(), cs.end());
+            const int32_t slack = 2 * (cfg.align - 1);
+            std::vector<Stage> cand;
+            // (a) the span of home columns the tile uses (the C_k of its
+            // parts, consecutive in x_hat) when it fits, plus the list
+            {
+                int32_t lo = INT32_MAX, hi = -1;
+                for (int32_t c : cs)
+                    if (c >= h0 && c < h1) {
+                        lo = std::min(lo, c);
+                        hi = std::max(hi, c);
+                    }
+                Stage g;
+                if (hi >= 0) aligned_run(lo, hi, &g.run0, &g.runlen);
+                if (g.runlen <= cfg.W) {
+                    finish_stage(g, cs);
+                    if (g.entries() <= cfg.W) cand.push_back(std::move(g));
                 }
             }
-            const double line = 128.0 / cfg.entry_bytes;   // entries per 128-byte line
-            const double a_cost = (double)runlen / line + (double)a_list;
-            const bool a_fits = hi >= 0 && runlen + a_list <= cfg.W;
-            // option (b): every column used list_min times or more, the most used first
-            std::vector<int32_t> multi;
-            for (int32_t c : used)
-                if (cnt[c] >= cfg.list_min) multi.push_back(c);
-            if ((int64_t)multi.size() > cfg.W) {
-                std::nth_element(multi.begin(), multi.begin() + cfg.W, multi.end(),
-                                 [&](int32_t x, int32_t y) {
-                                     return cnt[x] != cnt[y] ? cnt[x] > cnt[y] : x < y;
-                                 });
-                multi.resize((size_t)cfg.W);
+            // (b) the list alone: the most used columns
+            {
+                Stage g;
+                finish_stage(g, cs);
+                cand.push_back(std::move(g));
             }
-            std::sort(multi.begin(), multi.end());
-            int64_t b_saved = 0;
-            for (int32_t c : multi) b_saved += cnt[c];
-            const double b_cost = (double)multi.size();
-            const double a_gain = a_fits ? (double)a_saved - a_cost : -1.0;
-            const double b_gain = (double)b_saved - b_cost;
-            const bool use_a = a_fits && a_gain >= b_gain;
-            const double gain = use_a ? a_gain : b_gain;
-            const double cost = use_a ? a_cost : b_cost;
-            // stage when it saves at least as many requests as it costs: a
+            // (c) the densest window of x_hat, then the densest window of
+            // what is left, then the list
+            {
+                Stage g;
+                int32_t lo, hi;
+                if (best_window(cs, cfg.W - slack, lam(), 0, 0, &lo, &hi) > 0) {
+                    aligned_run(lo, hi, &g.run0, &g.runlen);
+                    if (best_window(cs, cfg.W - g.runlen - cfg.align - slack, lam(), g.run0,
+                                    g.run0 + g.runlen, &lo, &hi) > 0)
+                        aligned_run(lo, hi, &g.run2_0, &g.run2len);
+                    // aligned runs may touch; they never overlap (the second
+                    // avoids the first's columns, and alignment rounds both
+                    // outward only to the same boundaries)
+                    if (g.run2len > 0 && g.run2_0 < g.run0 + g.runlen &&
+                        g.run0 < g.run2_0 + g.run2len) {
+                        g.run2_0 = g.run2len = 0;
+                    }
+                    finish_stage(g, cs);
+                    if (g.entries() <= cfg.W) cand.push_back(std::move(g));
+                }
+            }
+            const Stage *best = nullptr;
+            for (const Stage &g : cand)
+                if (g.entries() <= cfg.W && (!best || g.gain() > best->gain())) best = &g;
+            // stage when it saves at least as many gathers as it costs (a
             // staged entry is fetched before the tile's rows start, where its
-            // latency is not hidden
-            if (gain > 0.0 && gain >= cost) {
-                if (!use_a) run0 = runlen = 0;
-                int32_t pos = runlen, listlen = 0, direct = 0;
+            // latency is not hidden) and covers a quarter of the tile's
+            // uses: a tile that stages and still gathers issues a shared-
+            // memory load beside the gather in the slots that gather
+            if (best && best->gain() > 0.0 && best->gain() >= best->cost &&
+                4 * best->saved >= tile_nnz) {
+                const Stage &g = *best;
+                int32_t listlen = 0;
+                int64_t direct = 0;
                 t.list0 = (int32_t)P.xlist.size();
-                for (int32_t c : used) loc[c] = -1;
-                if (use_a) {
-                    for (int32_t c : used) {
-                        if (c >= run0 && c < run0 + runlen) loc[c] = c - run0;
-                        else if (cnt[c] >= cfg.list_min) {
-                            loc[c] = pos++;
-                            P.xlist.push_back(c);
-                            ++listlen;
-                        }
-                    }
-                } else {
-                    for (int32_t c : multi) {
-                        loc[c] = pos++;
-                        P.xlist.push_back(c);
-                        ++listlen;
-                    }
+                for (int32_t c : cs) {
+                    if (c >= g.run0 && c < g.run0 + g.runlen) loc[c] = c - g.run0;
+                    else if (c >= g.run2_0 && c < g.run2_0 + g.run2len)
+                        loc[c] = g.run2_at + (c - g.run2_0);
+                    else loc[c] = -1;
                 }
-                for (int32_t c : used)
+                for (int32_t c : g.list) {
+                    loc[c] = g.run2_at + g.run2len + listlen++;
+                    P.xlist.push_back(c);
+                }
+                for (int32_t c : cs)
                     if (loc[c] < 0) direct += cnt[c];
                 t.kind = direct == 0 ? TILE_NARROW : TILE_MIXED;
-                t.run0 = run0;
-                t.runlen = runlen;
+                t.run0 = g.run0;
+                t.runlen = g.runlen;
+                t.run2_0 = g.run2_0;
+                t.run2len = g.run2len;
+                t.run2_at = g.run2_at;
                 t.listlen = listlen;
-                const int32_t staged = runlen + listlen;
+                const int32_t staged = g.entries();
                 P.max_staged = std::max(P.max_staged, staged);
                 P.staged_entries += staged;
                 P.list_entries += listlen;
@@ -384,12 +485,35 @@ struct Tiler {
             P.fma_slots += ((len + 31) / 32) * 32;
         }
         t.nvrows = (int32_t)P.vrows.size() - t.vrow0;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-            return prp[a + 1] - prp[a] > prp[b + 1] - prp[b];
-        });
+        // chunk rows by decreasing length; in MIXED tiles rows of equal
+        // length by decreasing count of gathered elements, so that the rows
+        // that gather share chunks and the others' chunks read shared memory
+        // only
+        std::vector<int32_t> ng;
+        if (t.kind == TILE_MIXED) {
+            ng.assign(order.size(), 0);
+            for (size_t k = 0; k < order.size(); ++k)
+                for (int32_t q = prp[order[k]]; q < prp[order[k] + 1]; ++q)
+                    ng[k] += loc[col[q]] < 0;
+            std::vector<int32_t> idx(order.size());
+            std::iota(idx.begin(), idx.end(), 0);
+            std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+                const int32_t la = prp[order[a] + 1] - prp[order[a]];
+                const int32_t lb = prp[order[b] + 1] - prp[order[b]];
+                return la != lb ? la > lb : ng[a] > ng[b];
+            });
+            std::vector<int32_t> o2(order.size());
+            for (size_t k = 0; k < idx.size(); ++k) o2[k] = order[idx[k]];
+            order.swap(o2);
+        } else {
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+                return prp[a + 1] - prp[a] > prp[b + 1] - prp[b];
+            });
+        }
         t.chunk0 = (int32_t)P.chunk_off.size();
         const int32_t nrows = (int32_t)order.size();
         t.nchunks = (nrows + 31) / 32;
+        std::vector<int32_t> seq;
         for (int32_t c = 0; c < t.nchunks; ++c) {
             const int32_t first = c * 32;
             const int32_t L = prp[order[first] + 1] - prp[order[first]];
@@ -400,6 +524,7 @@ struct Tiler {
             P.col16.resize(off + (size_t)L * 32, 0);
             P.padded_elems += (int64_t)L * 32;
             P.fma_slots += (int64_t)L * 32;
+            int32_t G = 0;
             for (int32_t i = 0; i < 32; ++i) {
                 const int32_t idx = first + i;
                 if (idx >= nrows) {
@@ -411,8 +536,23 @@ struct Tiler {
                 const int32_t a = prp[r], len = prp[r + 1] - a;
                 P.slot_dst.push_back(pdst[r]);
                 P.slot_len.push_back(len);
-                for (int32_t k = 0; k < len; ++k) put(off + (size_t)k * 32 + i, a + k);
+                // in MIXED tiles a row stores its gathered elements first, so
+                // that from slot G on (G = the most any row of the chunk
+                // gathers) every lane reads shared memory only
+                seq.clear();
+                if (t.kind == TILE_MIXED) {
+                    for (int32_t k = 0; k < len; ++k)
+                        if (loc[col[a + k]] < 0) seq.push_back(a + k);
+                    G = std::max(G, (int32_t)seq.size());
+                    for (int32_t k = 0; k < len; ++k)
+                        if (loc[col[a + k]] >= 0) seq.push_back(a + k);
+                } else {
+                    for (int32_t k = 0; k < len; ++k) seq.push_back(a + k);
+                }
+                for (int32_t k = 0; k < len; ++k) put(off + (size_t)k * 32 + i, seq[k]);
             }
+            P.chunk_mix.push_back(G);
+            P.mixed_slots += (int64_t)G * 32;
         }
         P.tiles.push_back(t);
     }
@@ -507,20 +647,24 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     // CTA shape: 6 CTAs of 256 threads per SM (fewer for 4 or 8 right-hand
     // sides), each staging up to 36 KB of x (they fit an SM's 228 KB next to some L1), or one wide
     // CTA of 1024 threads per SM staging up to 200 KB
-    if (o.cta_threads != 0 && o.cta_threads != 256 && o.cta_threads != 1024) {
-        set_error("cta_threads=%d: must be 0, 256 or 1024", o.cta_threads);
+    if (o.cta_threads != 0 && o.cta_threads != 256 && o.cta_threads != 512 &&
+        o.cta_threads != 1024) {
+        set_error("cta_threads=%d: must be 0, 256, 512 or 1024", o.cta_threads);
         return SPMV_E_INVALID;
     }
-    const bool wide = o.cta_threads == 1024;
-    if (wide && (o.flags & (SPMV_FLAG_SM_AFFINE | SPMV_FLAG_PERSISTENT))) {
-        set_error("cta_threads=1024 runs one CTA per tile (no persistent or SM-affine launch)");
+    const bool wide = o.cta_threads == 1024, mid = o.cta_threads == 512;
+    if ((wide || mid) && (o.flags & (SPMV_FLAG_SM_AFFINE | SPMV_FLAG_PERSISTENT))) {
+        set_error("cta_threads=%d runs one CTA per tile (no persistent or SM-affine launch)",
+                  o.cta_threads);
         return SPMV_E_INVALID;
     }
-    // tiles per SM of a launch: one wave of the 256-thread CTAs; four waves
-    // of wide CTAs (one per SM), so a slow tile does not hold up an SM
-    const int32_t ctas_per_sm = wide ? 4 : tile_ctas_per_sm_for(r);
-    int32_t W = o.tile_cols > 0 ? o.tile_cols
-                                : std::min<int32_t>(65535, ((wide ? 200 : 36) * 1024) / (xb * r));
+    // tiles per SM of a launch: one wave of the 256-thread CTAs; two waves
+    // of the 512-thread CTAs (two per SM) and four of the wide ones (one per
+    // SM), so that a slow tile does not hold up an SM
+    const int32_t ctas_per_sm = wide ? 4 : (mid ? 4 : tile_ctas_per_sm_for(r));
+    int32_t W = o.tile_cols > 0
+                    ? o.tile_cols
+                    : std::min<int32_t>(65535, ((wide ? 200 : (mid ? 96 : 36)) * 1024) / (xb * r));
     if ((int64_t)W * xb * r > 220 * 1024 || W > 65535) {
         set_error("tile_cols=%d does not fit shared memory (x entries of %d bytes, r=%d)", W,
                   xb, r);
@@ -533,7 +677,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     P->dtype = o.dtype;
     P->nrhs = r;
     if (o.flags & ~(SPMV_FLAG_NO_STAGING | SPMV_FLAG_TILED_NATURAL | SPMV_FLAG_SM_AFFINE |
-                    SPMV_FLAG_PERSISTENT | SPMV_FLAG_STAGE)) {
+                    SPMV_FLAG_PERSISTENT | SPMV_FLAG_STAGE | SPMV_FLAG_TEST_WAIT_EXPIRES)) {
         set_error("unknown flag bits 0x%x", o.flags);
         return SPMV_E_INVALID;
     }
@@ -542,7 +686,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         return SPMV_E_INVALID;
     }
     P->flags = o.flags;
-    P->cta_threads = o.cta_threads == 1024 ? 1024 : 256;
+    P->cta_threads = o.cta_threads == 1024 ? 1024 : (o.cta_threads == 512 ? 512 : 256);
     P->tile_cols = W;
 
     // permutation
@@ -715,7 +859,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         cfg.chunk = std::max<int32_t>(4096, cfg.tnnz / 4);
         cfg.long_t = o.long_row > 0 ? o.long_row : std::max<int32_t>(1024, cfg.tnnz / 16);
     }
-    cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING) && (wide || (o.flags & SPMV_FLAG_STAGE));
+    cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING) && (wide || mid || (o.flags & SPMV_FLAG_STAGE));
     P->lanes = 32;                 // one lane per row, 32 rows per chunk
     P->long_thresh = cfg.long_t;
 

@@ -85,11 +85,11 @@ def test_plan_create_validation_before_any_device_call():
     assert _plan_status(tile_cols=1 << 20)[0] == S.SPMV_E_UNSUPPORTED
     st, msg = _plan_status(warp_rows=-1)
     assert st == S.SPMV_E_INVALID and "warp_rows" in msg
-    st, msg = _plan_status(cta_threads=512)
+    st, msg = _plan_status(cta_threads=384)
     assert st == S.SPMV_E_INVALID and "cta_threads" in msg
     st, msg = _plan_status(cta_threads=1024, flags=S.SPMV_FLAG_PERSISTENT | 2)
     assert st == S.SPMV_E_INVALID
-    st, msg = _plan_status(flags=32)
+    st, msg = _plan_status(flags=64)
     assert st == S.SPMV_E_INVALID and "flag" in msg
     st, msg = _plan_status(flags=S.SPMV_FLAG_SM_AFFINE | S.SPMV_FLAG_PERSISTENT)
     assert st == S.SPMV_E_INVALID and "flag" in msg.lower()

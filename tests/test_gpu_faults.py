@@ -1,7 +1,9 @@
 """Failure detection without a GPU fault: allocation failures injected on the
 host through the plan's allocator hook are reported as SPMV_E_NOMEM, leave
 nothing behind, and leave an existing plan usable; the status word of the
-bounded device waits reads clean after normal work."""
+bounded device waits reads clean after normal work, and a wait made to run
+out (a plan whose first wait on each staging copy polls zero times) is
+reported as SPMV_E_TIMEOUT with the context still usable."""
 import ctypes
 
 import numpy as np
@@ -90,3 +92,35 @@ def test_host_io_allocation_failure_leaves_the_plan_usable():
     S.spmv_plan_check(plan)
     S.spmv_plan_destroy(plan)
     assert not al.live
+
+
+def test_bounded_wait_that_runs_out_reports_timeout():
+    """The staged tiles of a plan built with SPMV_FLAG_TEST_WAIT_EXPIRES give
+    up their first wait at once: they raise the status word, wait (bounded)
+    for their copy and skip their rows.  spmv_plan_check reports
+    SPMV_E_TIMEOUT; the device stays usable for the next plan."""
+    import oracle
+    nx = 64
+    rp, ci, v = synth.mesh5(nx, seed=5)
+    m = n = nx * nx
+    lab = (np.arange(m) * 8 // m).astype(np.int32)
+    rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SB, 8, lab)
+    kw = dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SB, K=8, row_part_ptr=rpp,
+              col_part_ptr=cpp, tile_nnz=2048)
+    bad = S.spmv_plan_create(m, n, rp, ci, v,
+                             flags=S.SPMV_FLAG_STAGE | S.SPMV_FLAG_TEST_WAIT_EXPIRES, **kw)
+    assert bad.info["n_staged_tiles"] > 0
+    x = torch.from_numpy(synth.uniform_x(n, 6)).cuda()
+    y = torch.empty(m, dtype=torch.float64, device="cuda")
+    S.spmv_exec(bad, x, y)
+    with pytest.raises(S.SpmvError) as e:
+        S.spmv_plan_check(bad)
+    assert e.value.status == S.SPMV_E_TIMEOUT
+    S.spmv_plan_destroy(bad)
+    good = S.spmv_plan_create(m, n, rp, ci, v, flags=S.SPMV_FLAG_STAGE, **kw)
+    xs = synth.uniform_x(n, 7)
+    y = run_plan(S, good, xs)
+    y_ref, absax = oracle.spmv(m, n, rp, ci, v, xs)
+    assert np.all(np.abs(y - y_ref) <= 1e-12 * absax)
+    S.spmv_plan_check(good)
+    S.spmv_plan_destroy(good)

@@ -188,19 +188,43 @@ def test_staged_runs_persistent_repeat(flags):
         _check(plan, m, n, rp, ci, vi, synth.integer_x(n, seed), exact=True)
 
 
+@pytest.mark.parametrize("cta", [512, 1024])
 @pytest.mark.parametrize("nrhs", [1, 8])
 @pytest.mark.parametrize("dtype", [0, 2])
-def test_wide_ctas_exact(zipf, dtype, nrhs):
-    # one 1024-thread CTA per tile with a large staging window
+def test_wide_ctas_exact(zipf, dtype, nrhs, cta):
+    # 512-thread (two per SM) and 1024-thread (one per SM) CTAs per tile with
+    # large staging windows
     m, n, rp, ci, _ = zipf
     vi = synth.integer_values(int(rp[-1]), 31)
     x = synth.integer_x(n, 32, nrhs=nrhs)
-    for plan in (_sb_plan(m, n, rp, ci, vi, 8, 33, dtype=dtype, nrhs=nrhs, cta_threads=1024),
-                 _split_plan(m, n, rp, ci, vi, 16, 34, dtype=dtype, nrhs=nrhs, cta_threads=1024,
+    for plan in (_sb_plan(m, n, rp, ci, vi, 8, 33, dtype=dtype, nrhs=nrhs, cta_threads=cta),
+                 _split_plan(m, n, rp, ci, vi, 16, 34, dtype=dtype, nrhs=nrhs, cta_threads=cta,
                              tile_nnz=8192),
-                 S.spmv_plan_create(m, n, rp, ci, vi, dtype=dtype, nrhs=nrhs, cta_threads=1024,
+                 S.spmv_plan_create(m, n, rp, ci, vi, dtype=dtype, nrhs=nrhs, cta_threads=cta,
                                     flags=S.SPMV_FLAG_TILED_NATURAL, long_row=200)):
         _check(plan, m, n, rp, ci, vi, x, exact=True)
+
+
+@pytest.mark.parametrize("cta", [256, 512, 1024])
+@pytest.mark.parametrize("dtype,nrhs", [(0, 1), (1, 1), (2, 1), (0, 2), (1, 8)])
+def test_two_runs_and_mixed_prefix_exact(cta, dtype, nrhs):
+    """Tiles that stage the home columns and a window of the border (two
+    bulk copies) and still gather some entries: each chunk's leading slots
+    load from both memories, the rest from shared memory only.  The host
+    emulation of the same plan confirms the image has those features."""
+    m, n, rp, ci, kw = _mesh_sb(95, 32)
+    vi = synth.integer_values(int(rp[-1]), 37)
+    x = synth.integer_x(n, 38, nrhs=nrhs)
+    opts = dict(dtype=dtype, nrhs=nrhs, cta_threads=cta, tile_nnz=6000,
+                flags=S.SPMV_FLAG_STAGE if cta == 256 else 0)
+    _, st = S.spmv_plan_emulate(m, n, rp, ci, vi, np.asarray(x, dtype=np.float64), **opts,
+                                **kw)
+    assert st["mixed_slots"] > 0 and st["staged_tiles"] > 0
+    if nrhs == 1:
+        assert st["two_run_tiles"] > 0
+    assert 0 < st["gathered_nnz"] < int(rp[-1])
+    plan = S.spmv_plan_create(m, n, rp, ci, vi, **opts, **kw)
+    _check(plan, m, n, rp, ci, vi, x, exact=True)
 
 
 def test_wide_ctas_staged_mesh():

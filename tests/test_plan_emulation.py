@@ -15,7 +15,7 @@ import synth
 
 S = pytest.importorskip("paper_1203_2739_gb300")
 
-SHAPE_NAMES = ["cta256", "cta256w", "cta256s", "cta1024", "cta256x8"]
+SHAPE_NAMES = ["cta256", "cta256w", "cta256s", "cta512", "cta1024", "cta256x8"]
 
 
 def _integer(rp, ci, seed):
@@ -80,11 +80,20 @@ def test_every_form_and_shape(name):
     st = _check(m, n, rp, ci, v, x, y_ref)
     assert st["plain_csr"] == 1
     seen = {"chunk_tiles": 0, "staged_tiles": 0, "partial_slots": 0, "warp_rows": 0}
+    forms = _forms(m, n, rp, ci, 64, 16, 7)
+    if name in ("mesh160", "blocks16"):
+        # a partitioner-made SB form: parts with local columns, which the
+        # tiles stage
+        part = S.spmv_partition(m, n, rp, ci, S.SPMV_PART_CN, K=16, seed=0)
+        forms.append(("sb-cn", dict(row_perm=part["row_perm"], col_perm=part["col_perm"],
+                                    form=part["form"], K=part["K"],
+                                    row_part_ptr=part["row_part_ptr"],
+                                    col_part_ptr=part["col_part_ptr"])))
     for shape in SHAPE_NAMES:
         st = _check(m, n, rp, ci, v, x, y_ref, flags=S.SPMV_FLAG_TILED_NATURAL |
                     shapes[shape].get("flags", 0),
                     **{k: a for k, a in shapes[shape].items() if k != "flags"})
-        for form, kw in _forms(m, n, rp, ci, 64, 16, 7):
+        for form, kw in forms:
             st = _check(m, n, rp, ci, v, x, y_ref, **shapes[shape], **kw)
             assert st["plain_csr"] == 0 and st["tiles"] > 0
             for k in seen:
@@ -95,7 +104,7 @@ def test_every_form_and_shape(name):
     assert seen["partial_slots"] > 0
     if name in ("zipf16k", "rmat15"):
         assert seen["warp_rows"] > 0
-    if name in ("mesh160", "blocks16"):
+    if name == "mesh160":
         assert seen["staged_tiles"] > 0
     # rows over the long-row threshold become chunk tiles (R-MAT's hubs;
     # forced on the Zipf matrix with a low threshold)
@@ -119,7 +128,7 @@ def test_precision_layouts_and_right_hand_sides(dtype, nrhs):
     x = synth.integer_x(n, 9, nrhs=nrhs) if nrhs > 1 else synth.integer_x(n, 9)
     y_ref = _reference(m, n, rp, ci, v, x)
     shapes = bench.tile_shapes(S, dtype, nrhs, int(rp[-1]))
-    for shape in ("cta256", "cta256s", "cta1024"):
+    for shape in ("cta256", "cta256s", "cta512", "cta1024"):
         for form, kw in _forms(m, n, rp, ci, 32, 16, 10):
             _check(m, n, rp, ci, v, x, y_ref, **shapes[shape], **kw)
 
