@@ -592,14 +592,20 @@ def run_ours(args, rank, world, local_rank):
                 plan = batched_split_plan(S, name, int(f[11:]), dtype, threads, nrhs=r)
             elif f in ("natural", "random") or args.no_autotune:
                 plan = S.spmv_plan_create(m, n, rp, ci, v, dtype=dtype, nrhs=r, **kw)
-            elif args.shape:
-                plan = S.spmv_plan_create(m, n, rp, ci, v, **shapes[args.shape], **kw)
-                chosen = args.shape
             else:
-                names = list(shapes)
-                plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v,
-                                                      [shapes[k] for k in names], reps=5, **kw)
-                chosen = names[ibest]
+                # the form's own flags (natural order through the tiled
+                # kernel) join each shape's
+                fl = kw.pop("flags", 0)
+                shapes = {k: dict(c, flags=c.get("flags", 0) | fl) for k, c in shapes.items()}
+                if args.shape:
+                    plan = S.spmv_plan_create(m, n, rp, ci, v, **shapes[args.shape], **kw)
+                    chosen = args.shape
+                else:
+                    names = list(shapes)
+                    plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v,
+                                                          [shapes[k] for k in names], reps=5,
+                                                          **kw)
+                    chosen = names[ibest]
             xh = torch.empty_like(xt)
             S.spmv_permute_x(plan, xt, xh)
             yh = torch.empty((m, r) if r > 1 else m, dtype=tdt, device=dev)

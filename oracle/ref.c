@@ -15,7 +15,9 @@
  *                       CPU baseline; with OpenMP (when the build has it) the
  *                       rows are shared among host threads.
  *   ref_permute_csr     A_hat = P_r A P_c (Sec. 3, first paragraph).
- *   ref_form_rows       SB form (eqs. 1-3) / DB form (eq. 5) from row labels.
+ *   ref_form_rows       SB form (eqs. 1-3) / DB form (eq. 5) from row labels;
+ *                       coupling columns grouped by the part holding most of
+ *                       their nonzeros (Sec. 3, similar patterns nearby).
  *   ref_form_split      row/column order of a split (Sec. 4) by first-touching part.
  *   ref_split_parts     the A^k matrices of a split in GCSR (Sec. 4, Sec. 5.2).
  *   ref_lambda_rows     lambda(c_j) over row parts (eq. 3; lambda' for DB).
@@ -239,6 +241,55 @@ void ref_lambda_split(int32_t m, int32_t n, const int64_t *rowptr,
  * Perms map new -> old.  row_part_ptr/col_part_ptr have K+2 entries:
  * R_k = [p[k], p[k+1]), R_B = [p[K], p[K+1]); likewise C_k and C_B.
  * Returns 0, or -1 on a label outside the allowed range. */
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* For each column, the part (label < K) holding most of its nonzeros, the
+ * lower part on ties; K for a column no non-border row touches.  The order
+ * of the coupling columns inside the border is not fixed by eqs. (1)-(2) or
+ * (5); Sec. 3 asks that columns with similar sparsity patterns be placed near
+ * each other, so the border groups its columns by this part.  Plain: the
+ * labels of each column's rows are collected, sorted and counted. */
+int32_t *ref_majority_part(int32_t m, int32_t n, const int64_t *rowptr,
+                           const int32_t *col, int32_t K, const int32_t *labels)
+{
+    int64_t *cstart = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < m; ++i)
+        if (labels[i] < K)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) cstart[col[p] + 1]++;
+    for (int32_t j = 0; j < n; ++j) cstart[j + 1] += cstart[j];
+    int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * ((size_t)cstart[n] + 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    for (int32_t j = 0; j < n; ++j) fill[j] = cstart[j];
+    for (int32_t i = 0; i < m; ++i)
+        if (labels[i] < K)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) lab[fill[col[p]]++] = labels[i];
+    int32_t *maj = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t j = 0; j < n; ++j) {
+        int64_t a = cstart[j], b = cstart[j + 1];
+        qsort(lab + a, (size_t)(b - a), sizeof(int32_t), cmp_i32);
+        int32_t best = K;
+        int64_t best_cnt = 0;
+        for (int64_t p = a; p < b;) {
+            int64_t q = p;
+            while (q < b && lab[q] == lab[p]) ++q;
+            if (q - p > best_cnt) {     /* strictly more: ties keep the lower part */
+                best_cnt = q - p;
+                best = lab[p];
+            }
+            p = q;
+        }
+        maj[j] = best;
+    }
+    free(cstart);
+    free(lab);
+    free(fill);
+    return maj;
+}
+
 int32_t ref_form_rows(int32_t m, int32_t n, const int64_t *rowptr,
                       const int32_t *col, int32_t K, const int32_t *labels,
                       int32_t border, int32_t *row_perm, int32_t *col_perm,
@@ -266,11 +317,16 @@ int32_t ref_form_rows(int32_t m, int32_t n, const int64_t *rowptr,
             if (lam[j] == 1 && one[j] == k) col_perm[t++] = j;
     }
     col_part_ptr[K] = t;
-    for (int32_t j = 0; j < n; ++j)
-        if (lam[j] >= 2) col_perm[t++] = j;
+    /* coupling columns (lambda >= 2) by the part holding most of their
+     * nonzeros, then by index; untouched columns last, by index */
+    int32_t *maj = ref_majority_part(m, n, rowptr, col, K, labels);
+    for (int32_t k = 0; k < K; ++k)
+        for (int32_t j = 0; j < n; ++j)
+            if (lam[j] >= 2 && maj[j] == k) col_perm[t++] = j;
     for (int32_t j = 0; j < n; ++j)
         if (lam[j] == 0) col_perm[t++] = j;
     col_part_ptr[K + 1] = n;
+    free(maj);
     free(lam);
     free(one);
     return 0;

@@ -1030,8 +1030,53 @@ spmv_status form_from_labels(const spmv_csr *A, int32_t form, int32_t K,
         for (int32_t k = 0; k <= K + 1; ++k) ccnt[k + 1] += ccnt[k];
         for (int32_t k = 0; k <= K; ++k) col_part_ptr[k] = ccnt[k];
         col_part_ptr[K + 1] = n;
+        // The border's coupling columns go by the part holding most of their
+        // nonzeros (the lower part on ties), then by index: columns used
+        // mostly by the same part sit together (Sec. 3 places columns with
+        // similar sparsity patterns near each other), so a part's border
+        // columns form a few contiguous ranges of x_hat that a tile can
+        // stage in bulk.  Untouched columns follow, by index.
+        std::vector<int32_t> maj((size_t)n, K);
+        {
+            std::vector<int64_t> cstart((size_t)n + 1, 0);
+            for (int32_t i = 0; i < m; ++i)
+                if (labels[i] < K)
+                    for (int32_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
+                        if (multi[A->colidx[p]]) cstart[A->colidx[p] + 1]++;
+            for (int32_t c = 0; c < n; ++c) cstart[c + 1] += cstart[c];
+            std::vector<int32_t> lab((size_t)cstart[n]);
+            std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+            for (int32_t i = 0; i < m; ++i)
+                if (labels[i] < K)
+                    for (int32_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
+                        if (multi[A->colidx[p]]) lab[(size_t)fill[A->colidx[p]]++] = labels[i];
+            for (int32_t c = 0; c < n; ++c) {
+                if (!multi[c]) continue;
+                auto a = lab.begin() + cstart[c], b = lab.begin() + cstart[c + 1];
+                std::sort(a, b);
+                int64_t best = 0;
+                for (auto q = a; q != b;) {
+                    auto r = q;
+                    while (r != b && *r == *q) ++r;
+                    if (r - q > best) {
+                        best = r - q;
+                        maj[c] = *q;
+                    }
+                    q = r;
+                }
+            }
+        }
         std::vector<int32_t> pos(ccnt.begin(), ccnt.end() - 1);
-        for (int32_t c = 0; c < n; ++c) col_perm[pos[cls(c)]++] = c;
+        for (int32_t c = 0; c < n; ++c)
+            if (cls(c) != K) col_perm[pos[cls(c)]++] = c;
+        {
+            std::vector<int32_t> mc((size_t)K + 1, 0);
+            for (int32_t c = 0; c < n; ++c)
+                if (cls(c) == K) mc[maj[c] + 1]++;
+            for (int32_t k = 0; k < K; ++k) mc[k + 1] += mc[k];
+            for (int32_t c = 0; c < n; ++c)
+                if (cls(c) == K) col_perm[ccnt[K] + mc[maj[c]]++] = c;
+        }
         return SPMV_OK;
     }
     if (form == SPMV_SPLIT) {

@@ -184,6 +184,19 @@ def test_db_form_golden():
     assert bad == 0
 
 
+@pytest.mark.parametrize("which", ["sb", "db"])
+def test_border_order_golden(which):
+    """The order of the coupling columns inside the border, hand-derived
+    (tests/golden/forms_small.json, "border_order")."""
+    g = _golden("forms_small.json")["border_order"]
+    m, n, rp, ci, v = _small_from_rows(g)
+    s = g[which]
+    rperm, cperm, rptr, cptr = oracle.form_rows(m, n, rp, ci, s["K"], s["labels"],
+                                                border=which == "db")
+    assert rperm.tolist() == s["row_perm"] and rptr.tolist() == s["row_part_ptr"]
+    assert cperm.tolist() == s["col_perm"] and cptr.tolist() == s["col_part_ptr"]
+
+
 def test_split_golden():
     g = _golden("forms_small.json")
     m, n, rp, ci, v = _small_from_rows(g)
@@ -228,7 +241,13 @@ def test_row_forms_bruteforce(seed, border):
                   any(A[i, j] != 0 and labels[i] == k for i in range(m))]
         assert ck == expect
     cb = cperm[cptr[K]:cptr[K + 1]].tolist()
-    assert cb == [j for j in range(n) if lam[j] >= 2] + [j for j in range(n) if lam[j] == 0]
+    # the border: coupling columns by the part holding most of their
+    # nonzeros (lower part on ties), then index; untouched columns last
+    def majority(j):
+        cnt = [sum(1 for i in range(m) if A[i, j] != 0 and labels[i] == k) for k in range(K)]
+        return max(range(K), key=lambda k: (cnt[k], -k))
+    assert cb == sorted((j for j in range(n) if lam[j] >= 2), key=lambda j: (majority(j), j)) \
+        + [j for j in range(n) if lam[j] == 0]
     # structure rule by brute force on the permuted dense matrix
     Ah = A[rperm][:, cperm]
     for k in range(K):
