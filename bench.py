@@ -279,13 +279,14 @@ def form_kwargs(S, f, rp, ci, parts, seed=0):
 def tile_shapes(S, dtype, nrhs, nnz):
     """The launch shapes the autotuner chooses from for a tiled plan: one
     wave of 256-thread tiles (rows over 64, or over 128, nonzeros reduced by
-    a warp; or staging x), 512-thread tiles (two per SM, 96 KB windows),
-    wide 1024-thread tiles (one per SM, 200 KB windows), or eight waves of
+    a warp), 512-thread tiles (two per SM, 48 KB shared-memory windows),
+    wide 1024-thread tiles (one per SM, 96 KB windows), or eight waves of
     smaller tiles (launched in order, so that the x windows of the tiles
-    running at once stay within L2 when x does not)."""
+    running at once stay within L2 when x does not).  Staging in the
+    256-thread tiles (SPMV_FLAG_STAGE) measured two to three times slower on
+    the sweep and is left out."""
     return {"cta256": dict(dtype=dtype, nrhs=nrhs),
             "cta256w": dict(dtype=dtype, nrhs=nrhs, warp_rows=128),
-            "cta256s": dict(dtype=dtype, nrhs=nrhs, flags=S.SPMV_FLAG_STAGE),
             "cta512": dict(dtype=dtype, nrhs=nrhs, cta_threads=512),
             "cta1024": dict(dtype=dtype, nrhs=nrhs, cta_threads=1024),
             "cta256x8": dict(dtype=dtype, nrhs=nrhs, tile_nnz=max(1024, nnz // (8 * 912)))}
@@ -603,7 +604,7 @@ def run_ours(args, rank, world, local_rank):
                 else:
                     names = list(shapes)
                     plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v,
-                                                          [shapes[k] for k in names], reps=5,
+                                                          [shapes[k] for k in names], reps=9,
                                                           **kw)
                     chosen = names[ibest]
             xh = torch.empty_like(xt)
@@ -1019,8 +1020,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="tiled forms with the default tile shape instead of the autotuned one")
-    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256w", "cta256s", "cta512",
-                                                    "cta1024", "cta256x8"],
+    ap.add_argument("--shape", default="", choices=["", "cta256", "cta256w", "cta512", "cta1024",
+                                                    "cta256x8"],
                     help="tiled forms with this tile shape instead of the autotuned one")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")

@@ -326,11 +326,13 @@ spmv_status spmv_mlp_adam(const spmv_mlp *net, const float *grads, float *m, flo
 
 /* Autotuner (not in the paper; the shapes the paper leaves to OSKI are picked
  * by measurement here): build one plan per candidate option set for the same
- * A / perm / splits, time `reps` calls of each on `stream` after one warm
- * call (zero input vectors, allocated from the first candidate's allocator
- * and released before returning), keep the fastest and destroy the others.
- * *best receives the index of the kept candidate, *best_ms its mean time per
- * call.  Synchronous.  Errors as spmv_plan_create, plus SPMV_E_CUDA. */
+ * A / perm / splits (all of them live at once), make one warm call of each,
+ * then `reps` rounds of one timed call per candidate in turn on `stream`
+ * (zero input vectors, allocated from the first candidate's allocator and
+ * released before returning), keep the candidate with the smallest median
+ * call and destroy the others.  *best receives the index of the kept
+ * candidate, *best_ms its median time per call.  Synchronous.  Errors as
+ * spmv_plan_create, plus SPMV_E_CUDA. */
 spmv_status spmv_plan_autotune(const spmv_csr *A, const spmv_perm *perm,
                                const spmv_splits *splits, const spmv_opts *candidates,
                                int32_t n_candidates, int32_t reps, void *stream,

@@ -543,87 +543,86 @@ extern "C" spmv_status spmv_plan_autotune(const spmv_csr *A, const spmv_perm *pe
     *out = nullptr;
     if (reps < 1) reps = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    spmv_plan *keep = nullptr;
-    float keep_ms = 0.0f;
-    int32_t keep_i = -1;
+    std::vector<spmv_plan *> plans;
+    std::vector<cudaEvent_t> ev;
     void *xb = nullptr, *yb = nullptr;
-    spmv_plan *owner = nullptr;          // plan whose allocator holds xb / yb
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
     spmv_status st = SPMV_OK;
-    auto fail_cuda = [&](cudaError_t e, const char *what) {
-        st = cuda_fail(e, what);
-        return st;
+    int32_t keep_i = -1;
+    float keep_ms = 0.0f;
+    auto cleanup = [&](int32_t keep) {
+        if (!plans.empty()) {
+            cudaStreamSynchronize(s);
+            dev_free(plans[0], xb);      // the scratch vectors come from the first
+            dev_free(plans[0], yb);      // plan's allocator
+        }
+        for (size_t i = 0; i < plans.size(); ++i)
+            if ((int32_t)i != keep) spmv_plan_destroy(plans[i]);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
     };
-    cudaError_t e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreate");
-    for (int32_t i = 0; i < n_candidates && st == SPMV_OK; ++i) {
+    // every candidate plan is built first; then the timed calls go round
+    // robin over the candidates (each call finds the caches as the previous
+    // candidate left them, as in a sequence of different products) and each
+    // candidate is judged by its median call
+    for (int32_t i = 0; i < n_candidates; ++i) {
         spmv_plan *p = nullptr;
         st = spmv_plan_create(A, perm, splits, &candidates[i], &p);
-        if (st != SPMV_OK) break;
-        if (!xb) {
-            // zero vectors sized for any candidate (same m, n; widest r)
-            size_t xbytes = 0, ybytes = 0;
-            for (int32_t j = 0; j < n_candidates; ++j) {
-                const int rj = candidates[j].nrhs > 0 ? candidates[j].nrhs : 1;
-                const size_t el = candidates[j].dtype == SPMV_F64 ? 8 : 4;
-                xbytes = std::max(xbytes, (size_t)A->n * rj * el);
-                ybytes = std::max(ybytes, (size_t)A->m * rj * el);
-            }
-            owner = p;
-            xb = dev_alloc(p, xbytes);
-            yb = dev_alloc(p, ybytes);
-            if (!xb || !yb) {
-                set_error("device allocation for autotuning failed");
-                st = SPMV_E_NOMEM;
-                spmv_plan_destroy(p);
-                owner = nullptr;
-                break;
-            }
-            if ((e = cudaMemsetAsync(xb, 0, xbytes, s)) != cudaSuccess) {
-                fail_cuda(e, "clear x");
-                break;
-            }
+        if (st != SPMV_OK) {
+            cleanup(-1);
+            return st;
         }
-        // one warm call, then reps timed calls
-        if ((e = run(p, xb, yb, s)) != cudaSuccess || (e = cudaEventRecord(e0, s)) != cudaSuccess) {
-            fail_cuda(e, "autotune launch");
-            spmv_plan_destroy(p);
-            break;
-        }
-        for (int32_t k = 0; k < reps && e == cudaSuccess; ++k) e = run(p, xb, yb, s);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            fail_cuda(e, "autotune timing");
-            spmv_plan_destroy(p);
-            break;
-        }
-        ms /= (float)reps;
-        if (!keep || ms < keep_ms) {
-            if (keep && keep != owner) spmv_plan_destroy(keep);
-            keep = p;
-            keep_ms = ms;
-            keep_i = i;
-        } else if (p != owner) {
-            spmv_plan_destroy(p);
-        }
+        plans.push_back(p);
     }
-    // the scratch vectors belong to the first plan's allocator
-    if (owner) {
-        cudaStreamSynchronize(s);
-        dev_free(owner, xb);
-        dev_free(owner, yb);
-        if (owner != keep) spmv_plan_destroy(owner);
+    size_t xbytes = 0, ybytes = 0;
+    for (int32_t j = 0; j < n_candidates; ++j) {
+        const int rj = candidates[j].nrhs > 0 ? candidates[j].nrhs : 1;
+        const size_t el = candidates[j].dtype == SPMV_F64 ? 8 : 4;
+        xbytes = std::max(xbytes, (size_t)A->n * rj * el);
+        ybytes = std::max(ybytes, (size_t)A->m * rj * el);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != SPMV_OK) {
-        if (keep) spmv_plan_destroy(keep);
+    xb = dev_alloc(plans[0], xbytes);
+    yb = dev_alloc(plans[0], ybytes);
+    if (!xb || !yb) {
+        set_error("device allocation for autotuning failed");
+        cleanup(-1);
+        return SPMV_E_NOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(xb, 0, xbytes, s);
+    ev.assign((size_t)2 * n_candidates * reps, nullptr);
+    for (size_t k = 0; k < ev.size() && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    for (int32_t i = 0; i < n_candidates && e == cudaSuccess; ++i) e = run(plans[i], xb, yb, s);
+    for (int32_t k = 0; k < reps && e == cudaSuccess; ++k)
+        for (int32_t i = 0; i < n_candidates && e == cudaSuccess; ++i) {
+            const size_t q = 2 * ((size_t)k * n_candidates + i);
+            e = cudaEventRecord(ev[q], s);
+            if (e == cudaSuccess) e = run(plans[i], xb, yb, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[q + 1], s);
+        }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "autotune timing");
+        cleanup(-1);
         return st;
     }
+    for (int32_t i = 0; i < n_candidates; ++i) {
+        std::vector<float> t((size_t)reps);
+        for (int32_t k = 0; k < reps && e == cudaSuccess; ++k) {
+            const size_t q = 2 * ((size_t)k * n_candidates + i);
+            e = cudaEventElapsedTime(&t[k], ev[q], ev[q + 1]);
+        }
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "autotune timing");
+            cleanup(-1);
+            return st;
+        }
+        std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+        const float med = t[reps / 2];
+        if (keep_i < 0 || med < keep_ms) {
+            keep_i = i;
+            keep_ms = med;
+        }
+    }
+    spmv_plan *keep = plans[keep_i];
+    cleanup(keep_i);
     *out = keep;
     if (best) *best = keep_i;
     if (best_ms) *best_ms = keep_ms;

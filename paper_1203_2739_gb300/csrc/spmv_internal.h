@@ -122,7 +122,13 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
 
 // Resident 256-thread CTAs per SM the tiled kernel is sized for (its
 // register budget asks for at least this many), by right-hand-side count.
-inline int32_t tile_ctas_per_sm_for(int32_t r) { return r <= 2 ? 6 : (r == 4 ? 4 : 3); }
+#ifndef SPMV_TILE_MINBLOCKS
+#define SPMV_TILE_MINBLOCKS 6
+#endif
+inline int32_t tile_ctas_per_sm_for(int32_t r)
+{
+    return r <= 2 ? SPMV_TILE_MINBLOCKS : (r == 4 ? 4 : 3);
+}
 
 // Round-to-nearest-even FP64 -> BF16 bits.
 uint16_t bf16_rne(double v);

@@ -62,6 +62,11 @@ constexpr int kWideThreads = 1024;
 #ifndef SPMV_WIDE_U
 #define SPMV_WIDE_U 8
 #endif
+//   SPMV_U256         elements per lane in flight per batch in the 256-thread
+//                     CTAs (one right-hand side; a power of two up to 16)
+#ifndef SPMV_U256
+#define SPMV_U256 8
+#endif
 //   SPMV_L1_PREF      1 = ask for the largest L1 carveout for the tile kernels
 #ifndef SPMV_L1_PREF
 #define SPMV_L1_PREF 0
@@ -406,6 +411,12 @@ __device__ __forceinline__ void chunk_span(int32_t kb, int32_t ke, int64_t off, 
 {
     int32_t k0 = kb;
     for (; k0 + U <= ke; k0 += U) chunk_batch<FX, U, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+    if constexpr (U > 8) {
+        if ((ke - k0) & 8) {
+            chunk_batch<FX, 8, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+            k0 += 8;
+        }
+    }
     if constexpr (U > 4) {
         if ((ke - k0) & 4) {
             chunk_batch<FX, 4, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
@@ -494,7 +505,7 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
     };
     // elements per lane in flight per batch (the wider CTAs have the larger
     // register budget)
-    constexpr int U = (R == 1 ? (NT == kThreads ? 8 : SPMV_WIDE_U) : (R == 2 ? 4 : 2));
+    constexpr int U = (R == 1 ? (NT == kThreads ? SPMV_U256 : SPMV_WIDE_U) : (R == 2 ? 4 : 2));
     constexpr int FXW = KIND == TILE_NARROW ? FX_SMEM16 : (KIND == TILE_MIXED ? FX_MIXED : FX_GLOBAL);
 
     for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += NT / 32) {
@@ -888,8 +899,14 @@ cudaError_t launch_k1(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
 }
 
 template <int R, typename VT, typename XT>
-cudaError_t launch_tiled(const DevPlan &P, const XT *x, XT *y, cudaStream_t s)
+cudaError_t launch_tiled(const DevPlan &P0, const XT *x, XT *y, cudaStream_t s)
 {
+#ifdef SPMV_FORCE_SMEM
+    DevPlan P = P0;     // experiment: reserve shared memory the tiles do not use
+    P.smem_bytes = std::max(P.smem_bytes, (int32_t)SPMV_FORCE_SMEM);
+#else
+    const DevPlan &P = P0;
+#endif
     if (P.n_tiles > 0) {
         TileArgs<VT, XT> A;
         A.tiles = P.tiles;

@@ -658,13 +658,17 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
                   o.cta_threads);
         return SPMV_E_INVALID;
     }
-    // tiles per SM of a launch: one wave of the 256-thread CTAs; two waves
-    // of the 512-thread CTAs (two per SM) and four of the wide ones (one per
-    // SM), so that a slow tile does not hold up an SM
-    const int32_t ctas_per_sm = wide ? 4 : (mid ? 4 : tile_ctas_per_sm_for(r));
+    // tiles per SM of a launch: one wave of the 256-thread CTAs, two waves
+    // of the 512-thread CTAs (two per SM) and of the wide ones (one per SM).
+    // Windows: 96 KB for the wide CTAs and 48 KB for each 512-thread CTA,
+    // which leaves L1 about 128 KB for the entries gathered and for the
+    // matrix stream in flight (measured on GB300: the blocks matrix in SB
+    // form, one wide CTA per SM, 126.9 us with 128 KB windows, 122.6 us with
+    // 96 KB windows in twice larger tiles, 198.6 us with 200 KB windows)
+    const int32_t ctas_per_sm = wide ? 2 : (mid ? 4 : tile_ctas_per_sm_for(r));
     int32_t W = o.tile_cols > 0
                     ? o.tile_cols
-                    : std::min<int32_t>(65535, ((wide ? 200 : (mid ? 96 : 36)) * 1024) / (xb * r));
+                    : std::min<int32_t>(65535, ((wide ? 96 : (mid ? 48 : 36)) * 1024) / (xb * r));
     if ((int64_t)W * xb * r > 220 * 1024 || W > 65535) {
         set_error("tile_cols=%d does not fit shared memory (x entries of %d bytes, r=%d)", W,
                   xb, r);

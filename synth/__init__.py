@@ -151,8 +151,9 @@ def zipf_matrix(m=16384, n=16384, seed=0, s_rows=1.7498, dmax=512, s_cols=1.2):
     return coo_to_csr(m, n, rows, cols, vals)
 
 
-def mesh5(nx=1024, seed=0, permute=True):
-    """5-point stencil on an nx x nx grid, values U(-1,1)."""
+def mesh5(nx=1024, seed=0, permute=True, return_points=False):
+    """5-point stencil on an nx x nx grid, values U(-1,1).  With
+    return_points, also the grid point (gy * nx + gx) of every row."""
     rng = _rng(seed)
     N = nx * nx
     idx = np.arange(N, dtype=np.int64)
@@ -165,12 +166,15 @@ def mesh5(nx=1024, seed=0, permute=True):
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
     vals = rng.uniform(-1.0, 1.0, size=rows.size)
+    points = idx
     if permute:
         perm = rng.permutation(N)
         inv = np.empty_like(perm)
         inv[perm] = np.arange(N)
         rows, cols = inv[rows], inv[cols]
-    return coo_to_csr(N, N, rows, cols, vals)
+        points = perm
+    out = coo_to_csr(N, N, rows, cols, vals)
+    return out + (points,) if return_points else out
 
 
 def rmat(scale=20, deg=16, a=0.57, b=0.19, c=0.19, seed=0, chunk=1 << 22):

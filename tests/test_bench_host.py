@@ -89,11 +89,10 @@ def test_batch_members_match_the_serial_generator_and_are_split(tmp_path):
 
 def test_tile_shapes_are_the_autotuner_candidates():
     sh = bench.tile_shapes(S, S.SPMV_F32, 8, 36_000_000)
-    assert list(sh) == ["cta256", "cta256w", "cta256s", "cta512", "cta1024", "cta256x8"]
+    assert list(sh) == ["cta256", "cta256w", "cta512", "cta1024", "cta256x8"]
     assert all(c["dtype"] == S.SPMV_F32 and c["nrhs"] == 8 for c in sh.values())
     assert sh["cta256w"]["warp_rows"] == 128 and sh["cta1024"]["cta_threads"] == 1024
     assert sh["cta512"]["cta_threads"] == 512
-    assert sh["cta256s"]["flags"] == S.SPMV_FLAG_STAGE
     # eight waves of 152 SMs x 6 resident CTAs
     assert sh["cta256x8"]["tile_nnz"] == 36_000_000 // (8 * 912)
     assert bench.tile_shapes(S, 0, 1, 1000)["cta256x8"]["tile_nnz"] == 1024

@@ -28,8 +28,8 @@ MATRICES = {
     "rmat20_d16": lambda: synth.rmat(20, 16, seed=0),
     "blocks64_0.2pct": lambda: synth.blocks(seed=0),
 }
-# the tile shape of each (matrix, form): SB, DB, split; every shape the
-# autotuner chooses from appears, staged and unstaged
+# the tile shape of each (matrix, form): SB, DB, split; the autotuner's
+# shapes and the staged 256-thread shape, staged and unstaged
 SHAPES = {
     "mesh5_1024": ("cta256", "cta256s", "cta1024"),
     "rmat20_d16": ("cta256w", "cta256x8", "cta256s"),
@@ -87,6 +87,7 @@ def test_full_size_forms_and_shapes(name):
     rows = np.unique(np.r_[0, m - 1, rng.integers(0, m, 4096)])
     y_ref, absax = _sample_reference(m, n, rp, ci, v, x, rows)
     shapes = bench.tile_shapes(S, S.SPMV_F64, 1, nnz)
+    shapes["cta256s"] = dict(dtype=S.SPMV_F64, nrhs=1, flags=S.SPMV_FLAG_STAGE)
     plans = [("natural", S.spmv_plan_create(m, n, rp, ci, v))]
     for (form, kw), shape in zip(_forms(m, n, rp, ci), SHAPES[name]):
         plans.append(("%s/%s" % (form, shape), S.spmv_plan_create(m, n, rp, ci, v,

@@ -18,6 +18,13 @@ S = pytest.importorskip("paper_1203_2739_gb300")
 SHAPE_NAMES = ["cta256", "cta256w", "cta256s", "cta512", "cta1024", "cta256x8"]
 
 
+def _shapes(dtype, nrhs, nnz):
+    """The autotuner's shapes and the staged 256-thread shape."""
+    sh = bench.tile_shapes(S, dtype, nrhs, nnz)
+    sh["cta256s"] = dict(dtype=dtype, nrhs=nrhs, flags=S.SPMV_FLAG_STAGE)
+    return sh
+
+
 def _integer(rp, ci, seed):
     return synth.integer_values(int(rp[-1]), seed)
 
@@ -76,7 +83,7 @@ def test_every_form_and_shape(name):
     x = synth.integer_x(n, 6)
     y_ref = _reference(m, n, rp, ci, v, x)
     nnz = int(rp[-1])
-    shapes = bench.tile_shapes(S, S.SPMV_F64, 1, nnz)
+    shapes = _shapes(S.SPMV_F64, 1, nnz)
     st = _check(m, n, rp, ci, v, x, y_ref)
     assert st["plain_csr"] == 1
     seen = {"chunk_tiles": 0, "staged_tiles": 0, "partial_slots": 0, "warp_rows": 0}
@@ -127,7 +134,7 @@ def test_precision_layouts_and_right_hand_sides(dtype, nrhs):
     v = _integer(rp, ci, 8)
     x = synth.integer_x(n, 9, nrhs=nrhs) if nrhs > 1 else synth.integer_x(n, 9)
     y_ref = _reference(m, n, rp, ci, v, x)
-    shapes = bench.tile_shapes(S, dtype, nrhs, int(rp[-1]))
+    shapes = _shapes(dtype, nrhs, int(rp[-1]))
     for shape in ("cta256", "cta256s", "cta512", "cta1024"):
         for form, kw in _forms(m, n, rp, ci, 32, 16, 10):
             _check(m, n, rp, ci, v, x, y_ref, **shapes[shape], **kw)
@@ -164,7 +171,7 @@ def test_partitioner_forms_on_the_configured_small_matrix():
         if res["form"] == S.SPMV_SPLIT:
             kw["nz_part"] = res["labels"]
         for shape in SHAPE_NAMES:
-            _check(m, n, rp, ci, v, x, y_ref, **bench.tile_shapes(S, 0, 1, int(rp[-1]))[shape],
+            _check(m, n, rp, ci, v, x, y_ref, **_shapes(0, 1, int(rp[-1]))[shape],
                    **kw)
 
 
@@ -176,7 +183,7 @@ def test_full_size_mesh_in_every_shape():
     v = _integer(rp, ci, 17)
     x = synth.integer_x(n, 18)
     y_ref = _reference(m, n, rp, ci, v, x)
-    shapes = bench.tile_shapes(S, 0, 1, int(rp[-1]))
+    shapes = _shapes(0, 1, int(rp[-1]))
     forms = _forms(m, n, rp, ci, 1024, 16, 19)
     for shape in SHAPE_NAMES:
         for form, kw in forms:
