@@ -5,12 +5,14 @@ plan reading its own x_hat and writing its own y_hat (device-resident inputs).
 The default workload is the FP64 reordering sweep: three 1,048,576-row
 matrices (5-point 1024^2 mesh, randomly permuted; R-MAT a,b,c = .57,.19,.19
 with 16 nonzeros per row; 64 diagonal 16,384^2 blocks at 0.2% fill plus 5%
-random off-block nonzeros, shuffled), each in natural order, after a random
-symmetric permutation, in the 1D SB form (column-net bisection, K = 1024:
-about one part per resident CTA of a launch), the 2D DB form (enhanced
-row-column-net bisection, K = 1024) and as splits with K = 4, 16, 64, 256
-(row-column-net bisection; the smaller K are levels of the same recursion
-tree).
+random off-block nonzeros, shuffled), each in natural order and after a
+random symmetric permutation (through the plain CSR kernel and through the
+tiled kernel), in the paper's comparison orders (sBFS and sRCM on the
+bipartite graph, sHP_RN: row-net bisection, K = 1024), in the 1D SB form
+(column-net bisection, K = 1024: about one part per resident CTA of a
+launch), the 2D DB form (enhanced row-column-net bisection, K = 1024) and as
+splits with K = 4, 16, 64, 256 (row-column-net bisection; the smaller K are
+levels of the same recursion tree).
 
 Metric: compulsory-bytes SpMV throughput, GB/s = sum over the step of
 [nnz*(vb+4) + (m+1)*4 + n*xb + m*xb] / time (Sec. 2.2 streaming model), with
@@ -48,8 +50,8 @@ import synth  # noqa: E402
 # natural and random orders run through both the plain CSR kernel and the
 # tiled kernel ("tiled", "rtiled"), so that the gain of a reordering is
 # measured against the same kernel in the original order
-FORMS_SWEEP = ["natural", "random", "tiled", "rtiled", "sb1024", "db1024", "split4", "split16",
-               "split64", "split256"]
+FORMS_SWEEP = ["natural", "random", "tiled", "rtiled", "bfs", "rcm", "rn1024", "sb1024", "db1024",
+               "split4", "split16", "split64", "split256"]
 NATURAL_FORMS = ("natural", "random", "tiled", "rtiled")
 MATRICES = {
     "sweep": [("mesh5_1024", lambda: synth.mesh5(1024, seed=0)),
@@ -108,8 +110,9 @@ def _batch_matrix(name):
     return synth.block_diagonal(mats)
 WORKLOAD_TEXT = {
     "sweep": "FP64 reordering sweep: mesh 1024^2 (5-pt, permuted), R-MAT 2^20 deg 16, "
-             "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random, SB K=1024, "
-             "DB K=1024, split K=4/16/64/256",
+             "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random (plain CSR "
+             "and tiled kernel), sBFS, sRCM, sHP_RN K=1024, SB K=1024, DB K=1024, "
+             "split K=4/16/64/256",
     "zipf16k": "Zipf 16384^2 (rows P(d)~d^-1.7498 on [1,512], Zipf(1.2) columns), natural vs SB",
     "batching": "256 R-MAT matrices (rows log-uniform in [1024, 262144], power-of-two sizes, "
                 "degree U[8,32]) in one plan: natural block-diagonal vs batched split K=16 "
@@ -175,7 +178,17 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
             need[("ercn", int(f[2:]))] = (S.SPMV_PART_ERCN, int(f[2:]))
         elif f.startswith("split"):
             need[("rcn", 256)] = (S.SPMV_PART_RCN, 256)
+        elif f.startswith("rn"):
+            need[("rn", int(f[2:]))] = (S.SPMV_PART_RN, int(f[2:]))
     res = {}
+    # the breadth-first orders (sBFS, sRCM) take seconds: not cached
+    for f in forms:
+        if f in ("bfs", "rcm"):
+            t0 = time.perf_counter()
+            rperm, cperm = S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_BFS if f == "bfs"
+                                          else S.SPMV_ORDER_RCM)
+            res[(f, 0)] = dict(form=S.SPMV_NATURAL, K=1, row_perm=rperm, col_perm=cperm, cost=0,
+                               cost_cols=0, cost_rows=0, seconds=time.perf_counter() - t0)
 
     def path(key):
         return os.path.join(cache_dir, "%s_%s_K%d_s%d.npz" % (name, key[0], key[1], seed))
@@ -215,6 +228,11 @@ def load_partition(S, path, m, n, rp, ci):
     with np.load(path) as z:
         r = {k: z[k].item() for k in z.files if k != "labels"}
         lab = np.ascontiguousarray(z["labels"], dtype=np.int32)
+    if int(r["form"]) == S.SPMV_NATURAL:
+        # a row-net partition: column labels, nested separated block-diagonal
+        rperm, cperm = S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_SBD, int(r["K"]), lab)
+        r.update(labels=lab, row_perm=rperm, col_perm=cperm)
+        return r
     rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, int(r["form"]), int(r["K"]),
                                                      lab)
     r.update(labels=lab, row_perm=rperm, col_perm=cperm, row_part_ptr=rpp, col_part_ptr=cpp)
@@ -251,6 +269,12 @@ def form_kwargs(S, f, rp, ci, parts, seed=0):
         if f == "rtiled":
             kw["flags"] = S.SPMV_FLAG_TILED_NATURAL
         return kw, None
+    if f in ("bfs", "rcm") or f.startswith("rn"):
+        # the comparison orders of Sec. 5.1, natural form through the tiled
+        # kernel
+        r = parts[(f, 0) if f in ("bfs", "rcm") else ("rn", int(f[2:]))]
+        return dict(row_perm=r["row_perm"], col_perm=r["col_perm"],
+                    flags=S.SPMV_FLAG_TILED_NATURAL), r
     if f.startswith("sb") or f.startswith("db"):
         r = parts[("cn" if f.startswith("sb") else "ercn", int(f[2:]))]
         return dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"], K=r["K"],
@@ -793,7 +817,16 @@ def reorder_gains(detail):
             e["gain_over_tiled_natural"] = {
                 f: round(us["tiled"] / t, 3) for f, t in us.items()
                 if f not in ("natural", "random", "tiled")}
+            # the paper's Table 2: each method's time over the original
+            # order's, with the same kernel (lower is better)
+            e["normalized_time"] = {f: round(t / us["tiled"], 3) for f, t in us.items()
+                                    if f not in ("natural", "random", "tiled")}
         out[mat] = e
+    norm = [e["normalized_time"] for e in out.values() if "normalized_time" in e]
+    if norm:
+        forms = [f for f in norm[0] if all(f in d for d in norm)]
+        out["geomean_normalized_time"] = {
+            f: round(float(np.exp(np.mean([np.log(d[f]) for d in norm]))), 3) for f in forms}
     return out
 
 

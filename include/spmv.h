@@ -364,7 +364,14 @@ enum {
                              (cut-net removal) -> DB (sHP_eRCN, Sec. 3.2) */
     SPMV_PART_RCN = 2,    /* row-column-net model, connectivity metric on
                              both net types -> split (mHP_RCN, Sec. 4.1) */
-    SPMV_PART_RANDOM = 3  /* uniform random row labels -> SB (a baseline) */
+    SPMV_PART_RANDOM = 3, /* uniform random row labels -> SB (a baseline) */
+    SPMV_PART_RN = 4      /* row-net model (sHP_RN, Sec. 5.1, a baseline):
+                             columns are vertices, rows are nets (the
+                             column-net model of A^T); labels[n] are column
+                             parts, the form is SPMV_NATURAL with the nested
+                             separated block-diagonal order of spmv_reorder
+                             (SPMV_ORDER_SBD); cost = cost_rows = the sum
+                             over rows of their connectivity */
 };
 
 /* Stop rule of the recursive bisection (Sec. 5.1) */
@@ -409,6 +416,30 @@ typedef struct spmv_partition_out {
 spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_opts *opts,
                            spmv_partition_out *out);
 void spmv_partition_free(spmv_partition_out *out);
+
+/* Row and column orders of the paper's comparison methods (Sec. 5.1), host
+ * only, into caller-allocated row_perm[m] and col_perm[n] (new -> old),
+ * for a plan of form SPMV_NATURAL.  The bipartite graph of A has a vertex per
+ * row and per column and an edge per nonzero; ties go to the lower vertex
+ * (rows before columns, then by index).
+ *   SPMV_ORDER_BFS (sBFS): breadth-first search from row 0, neighbours in
+ *     increasing order; when the queue runs dry, from the lowest unvisited
+ *     vertex.  Rows and columns in visiting order.
+ *   SPMV_ORDER_RCM (sRCM): reverse Cuthill-McKee: per connected component
+ *     (in order of its lowest vertex), a pseudo-peripheral start by the
+ *     George-Liu procedure from the component's vertex of least degree,
+ *     unvisited neighbours enqueued by increasing degree; the whole visiting
+ *     sequence reversed.
+ *   SPMV_ORDER_SBD (the order of sHP_RN): col_labels[n] in [0, K), K a power
+ *     of two, are the leaves of a recursive bisection of the columns (left
+ *     subtree first); columns by (label, index); a row whose columns all lie
+ *     in leaf k goes to block k, a row whose labels span a..b (a < b) to the
+ *     separator of the bisection that split a from b, placed between that
+ *     bisection's two halves; empty rows last; ties by index.
+ * Errors: SPMV_E_INVALID (bad CSR, K, labels or method). */
+enum { SPMV_ORDER_BFS = 0, SPMV_ORDER_RCM = 1, SPMV_ORDER_SBD = 2 };
+spmv_status spmv_reorder(const spmv_csr *A, int32_t method, int32_t K,
+                         const int32_t *col_labels, int32_t *row_perm, int32_t *col_perm);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *spmv_last_error(void);

@@ -36,7 +36,8 @@ SPMV_NATURAL, SPMV_SB, SPMV_DB, SPMV_SPLIT = 0, 1, 2, 3
 SPMV_FLAG_NO_STAGING, SPMV_FLAG_TILED_NATURAL, SPMV_FLAG_SM_AFFINE = 1, 2, 4
 SPMV_FLAG_PERSISTENT, SPMV_FLAG_STAGE = 8, 16
 SPMV_FLAG_TEST_WAIT_EXPIRES = 32
-SPMV_PART_CN, SPMV_PART_ERCN, SPMV_PART_RCN, SPMV_PART_RANDOM = 0, 1, 2, 3
+SPMV_PART_CN, SPMV_PART_ERCN, SPMV_PART_RCN, SPMV_PART_RANDOM, SPMV_PART_RN = 0, 1, 2, 3, 4
+SPMV_ORDER_BFS, SPMV_ORDER_RCM, SPMV_ORDER_SBD = 0, 1, 2
 SPMV_FIT_CSR, SPMV_FIT_X = 0, 1
 
 STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_E_INVALID", 2: "SPMV_E_STRUCTURE", 3: "SPMV_E_NOMEM",
@@ -51,7 +52,7 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
            "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched", "spmv_features",
            "spmv_mlp_param_count", "spmv_mlp_work_bytes", "spmv_mlp_forward", "spmv_mlp_grad",
-           "spmv_mlp_adam", "spmv_plan_emulate")
+           "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder")
 SPMV_EMULATE_STATS = 13
 EMULATE_STATS = ("tiles", "chunk_tiles", "staged_tiles", "partial_slots", "fixups", "warp_rows",
                  "stored_chunk_elements", "plain_csr", "gathered_nnz", "fma_lanes",
@@ -175,6 +176,8 @@ def _load():
     L.spmv_plan_destroy.argtypes = [vp]
     L.spmv_form_from_labels.argtypes = [ctypes.POINTER(spmv_csr), ctypes.c_int32,
                                         ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p]
+    L.spmv_reorder.argtypes = [ctypes.POINTER(spmv_csr), ctypes.c_int32, ctypes.c_int32,
+                               _i32p, _i32p, _i32p]
     L.spmv_partition.argtypes = [ctypes.POINTER(spmv_csr), ctypes.POINTER(spmv_partition_opts),
                                  ctypes.POINTER(spmv_partition_out)]
     L.spmv_partition_free.argtypes = [ctypes.POINTER(spmv_partition_out)]
@@ -195,7 +198,7 @@ def _load():
                  "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
                  "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir",
                  "spmv_plan_create_batched", "spmv_features", "spmv_mlp_forward",
-                 "spmv_mlp_grad", "spmv_mlp_adam", "spmv_plan_emulate"):
+                 "spmv_mlp_grad", "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -595,6 +598,18 @@ def spmv_form_from_labels(m, n, rowptr, colidx, form, K, labels):
     _check(lib.spmv_form_from_labels(ctypes.byref(A), form, K, _ptr(lab), _ptr(rperm),
                                      _ptr(cperm), _ptr(rpp), _ptr(cpp)))
     return rperm, cperm, rpp, cpp
+
+
+def spmv_reorder(m, n, rowptr, colidx, method, K=0, col_labels=None):
+    """Row and column orders of the comparison methods (sBFS, sRCM, and the
+    nested separated block-diagonal order of sHP_RN from column labels):
+    (row_perm, col_perm), new -> old."""
+    A, keep = _csr_struct(m, n, rowptr, colidx, None)
+    lab = None if col_labels is None else _i32(col_labels)
+    rperm = np.empty(m, dtype=np.int32)
+    cperm = np.empty(n, dtype=np.int32)
+    _check(lib.spmv_reorder(ctypes.byref(A), method, K, _ptr(lab), _ptr(rperm), _ptr(cperm)))
+    return rperm, cperm
 
 
 def spmv_partition(m, n, rowptr, colidx, method, K=0, part_bytes=0, fit_rule=SPMV_FIT_CSR,

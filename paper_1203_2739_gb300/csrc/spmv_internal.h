@@ -139,6 +139,10 @@ spmv_status form_from_labels(const spmv_csr *A, int32_t form, int32_t K,
                              int32_t *col_perm, int32_t *row_part_ptr,
                              int32_t *col_part_ptr);
 
+// Row / column orders of the comparison methods (spmv_reorder).
+spmv_status reorder(const spmv_csr *A, int32_t method, int32_t K, const int32_t *labels,
+                    int32_t *row_perm, int32_t *col_perm);
+
 // Validate a host CSR (sorted unique columns, monotone rowptr).
 spmv_status validate_csr(const spmv_csr *A);
 

@@ -1172,6 +1172,90 @@ HG build_model(const spmv_csr *A, int method, i32 seg, std::vector<i32> *seg_of)
 
 using namespace spmv;
 
+namespace spmv {
+spmv_status order_sbd(const spmv_csr *A, int32_t K, const int32_t *labels, int32_t *row_perm,
+                      int32_t *col_perm);
+}
+
+// Row-net model (sHP_RN, Sec. 5.1): the columns are the vertices and the rows
+// the nets, which is the column-net model of the transpose; the columns are
+// ordered by part and the rows into the nested separated block-diagonal
+// form (order_sbd).
+static spmv_status partition_row_net(const spmv_csr *A, const spmv_partition_opts *opts,
+                                     spmv_partition_out *out)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const i32 m = A->m, n = A->n;
+    const i64 nnz = A->nnz;
+    std::vector<i32> tp((size_t)n + 1, 0), ti((size_t)nnz);
+    for (i64 p = 0; p < nnz; ++p) tp[(size_t)A->colidx[p] + 1]++;
+    for (i32 j = 0; j < n; ++j) tp[(size_t)j + 1] += tp[(size_t)j];
+    {
+        std::vector<i32> fill(tp.begin(), tp.end() - 1);
+        for (i32 i = 0; i < m; ++i)
+            for (i32 p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) ti[(size_t)fill[A->colidx[p]]++] = i;
+    }
+    std::vector<double> ones((size_t)nnz, 1.0);
+    spmv_csr At{n, m, nnz, tp.data(), ti.data(), ones.data()};
+    spmv_partition_opts o = *opts;
+    o.method = SPMV_PART_CN;
+    spmv_partition_out t{};
+    spmv_status st = spmv_partition(&At, &o, &t);
+    if (st != SPMV_OK) return st;
+    const i32 K = t.K;
+    std::vector<i32> labels(t.labels, t.labels + n);
+    const i64 cost = t.cost;
+    spmv_partition_free(&t);
+    out->row_perm = (i32 *)std::malloc(sizeof(i32) * (size_t)std::max(m, 1));
+    out->col_perm = (i32 *)std::malloc(sizeof(i32) * (size_t)std::max(n, 1));
+    out->row_part_ptr = (i32 *)std::malloc(sizeof(i32) * (size_t)(K + 2));
+    out->col_part_ptr = (i32 *)std::malloc(sizeof(i32) * (size_t)(K + 2));
+    out->labels = (i32 *)std::malloc(sizeof(i32) * std::max<size_t>(labels.size(), 1));
+    if (!out->row_perm || !out->col_perm || !out->row_part_ptr || !out->col_part_ptr ||
+        !out->labels) {
+        spmv_partition_free(out);
+        set_error("out of host memory");
+        return SPMV_E_NOMEM;
+    }
+    std::copy(labels.begin(), labels.end(), out->labels);
+    st = spmv::order_sbd(A, K, labels.data(), out->row_perm, out->col_perm);
+    if (st != SPMV_OK) {
+        spmv_partition_free(out);
+        return st;
+    }
+    // column parts: the label ranges; row parts: where each leaf's block
+    // of rows starts in the nested order (separators lie between blocks)
+    std::vector<i32> cc((size_t)K + 1, 0);
+    for (i32 j = 0; j < n; ++j) cc[(size_t)labels[j] + 1]++;
+    for (i32 k = 0; k < K; ++k) cc[(size_t)k + 1] += cc[(size_t)k];
+    for (i32 k = 0; k <= K; ++k) out->col_part_ptr[k] = cc[(size_t)k];
+    out->col_part_ptr[K + 1] = n;
+    {
+        i32 r = 0;
+        for (i32 k = 0; k < K; ++k) {
+            // first row (in the new order) whose columns lie in leaves >= k
+            while (r < m) {
+                const i32 i = out->row_perm[r];
+                i32 lo = K;
+                for (i32 p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
+                    lo = std::min(lo, labels[A->colidx[p]]);
+                if (A->rowptr[i] < A->rowptr[i + 1] && lo < k) ++r;
+                else break;
+            }
+            out->row_part_ptr[k] = r;
+        }
+        out->row_part_ptr[K] = out->row_part_ptr[K + 1] = m;
+    }
+    out->form = SPMV_NATURAL;
+    out->K = K;
+    out->n_labels = n;
+    out->cost = cost;
+    out->cost_rows = cost;
+    out->cost_cols = 0;
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return SPMV_OK;
+}
+
 extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_opts *opts,
                                       spmv_partition_out *out)
 {
@@ -1186,10 +1270,11 @@ extern "C" spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_op
         if (st != SPMV_OK) return st;
         const auto t0 = std::chrono::steady_clock::now();
         const int method = opts->method;
-        if (method < SPMV_PART_CN || method > SPMV_PART_RANDOM) {
+        if (method < SPMV_PART_CN || method > SPMV_PART_RN) {
             set_error("unknown partitioning method %d", method);
             return SPMV_E_INVALID;
         }
+        if (method == SPMV_PART_RN) return partition_row_net(A, opts, out);
         int depth = -1;
         if (opts->K > 0) {
             if ((opts->K & (opts->K - 1)) != 0) {
