@@ -472,14 +472,22 @@ __device__ __forceinline__ void warp_row(const VRow &row, const VT *__restrict__
     for (int c = 0; c < R; ++c) s[c] = group_sum<32>(s[c]);
 }
 
-// The rows of a tile after staging.  Warp w takes the warp rows w, w + NT/32,
-// ..., then the chunks w, w + NT/32, ...: lane i owns row i of a chunk and
-// runs one FMA chain over it.  A chunk's metadata (row lengths,
-// destinations, offset, mixed prefix) is loaded one chunk ahead, so a chunk
-// costs two dependent trips to memory (its stream, then its gathers).
+// The rows of a tile after staging, as a sequence of items: the warp rows
+// (longest first), then the chunks of 32 rows (longest first).  Warp w
+// starts with item w; with `claim` (a shared-memory counter at zero) each
+// warp then claims its next item from the counter as it starts the current
+// one, so the warps of the CTA finish together however the row lengths
+// vary (longest-first claiming); without it, warp w takes items w + k NT/32.
+// A chunk's metadata (row lengths, destinations, offset, mixed prefix) is
+// loaded when the chunk is claimed, one item ahead, so a chunk costs two
+// dependent trips to memory (its stream, then its gathers).
+struct ChunkMeta {
+    int32_t len, dst, off, mix;
+};
+
 template <int KIND, int R, typename VT, typename XT, int NT>
 __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> &A,
-                                          const XT *seg)
+                                          const XT *seg, int32_t *claim)
 {
     const int32_t *__restrict__ chunk_off = A.chunk_off;
     const int32_t *__restrict__ chunk_mix = A.chunk_mix;
@@ -492,6 +500,7 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
     const XT *__restrict__ x = A.x;
     XT *__restrict__ y = A.y;
     XT *__restrict__ partial = A.partial;
+    constexpr int NW = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     auto store = [&](int32_t d, const XT (&s)[R]) {
         if (d >= 0) {
@@ -508,47 +517,56 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
     constexpr int U = (R == 1 ? (NT == kThreads ? SPMV_U256 : SPMV_WIDE_U) : (R == 2 ? 4 : 2));
     constexpr int FXW = KIND == TILE_NARROW ? FX_SMEM16 : (KIND == TILE_MIXED ? FX_MIXED : FX_GLOBAL);
 
-    for (int32_t vr = t.vrow0 + warp; vr < t.vrow0 + t.nvrows; vr += NT / 32) {
-        const VRow row = vrows[vr];
-        XT s[R];
-        warp_row<FXW, U, R, VT, XT>(row, val, c32, c16, seg, x, s);
-        if (lane == 0) store(row.dst, s);
-    }
-
-    const int32_t cend = t.chunk0 + t.nchunks;
-    int32_t ch = t.chunk0 + warp;
-    int32_t len_n = 0, dst_n = -1, off_n = 0, mix_n = 0;
-    if (ch < cend) {
-        len_n = __ldg(slot_len + ch * 32 + lane);
-        dst_n = __ldg(slot_dst + ch * 32 + lane);
-        off_n = __ldg(chunk_off + ch);
-        if (KIND == TILE_MIXED) mix_n = __ldg(chunk_mix + ch);
-    }
-    for (; ch < cend; ch += NT / 32) {
-        const int32_t len = len_n, dst = dst_n, G = mix_n;
-        const int64_t off = (int64_t)off_n + lane;
-        const int32_t chn = ch + NT / 32;
-        if (chn < cend) {
-            len_n = __ldg(slot_len + chn * 32 + lane);
-            dst_n = __ldg(slot_dst + chn * 32 + lane);
-            off_n = __ldg(chunk_off + chn);
-            if (KIND == TILE_MIXED) mix_n = __ldg(chunk_mix + chn);
+    const int32_t nv = t.nvrows, nitems = t.nvrows + t.nchunks;
+    auto meta = [&](int32_t item) {
+        ChunkMeta mt{0, -1, 0, 0};
+        if (item >= nv && item < nitems) {
+            const int32_t ch = t.chunk0 + (item - nv);
+            mt.len = __ldg(slot_len + ch * 32 + lane);
+            mt.dst = __ldg(slot_dst + ch * 32 + lane);
+            mt.off = __ldg(chunk_off + ch);
+            if (KIND == TILE_MIXED) mt.mix = __ldg(chunk_mix + ch);
         }
-        const int32_t L = __shfl_sync(0xffffffffu, len, 0);   // rows sorted: lane 0 is longest
-        XT s[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) s[c] = XT(0);
-        if constexpr (KIND == TILE_MIXED) {
-            // rows store their gathered elements first: slots [0, G) may
-            // gather, slots [G, L) read shared memory only
-            chunk_span<FX_MIXED, U, R, VT, XT>(0, G, off, len, val, c32, c16, seg, x, s);
-            chunk_span<FX_SMEM32, U, R, VT, XT>(G, L, off, len, val, c32, c16, seg, x, s);
-        } else if constexpr (KIND == TILE_NARROW) {
-            chunk_span<FX_SMEM16, U, R, VT, XT>(0, L, off, len, val, c32, c16, seg, x, s);
+        return mt;
+    };
+    int32_t cur = warp;
+    ChunkMeta mc = meta(cur);
+    while (cur < nitems) {
+        int32_t nxt;
+        if (claim) {
+            int32_t v = 0;
+            if (lane == 0) v = atomicAdd(claim, 1);
+            nxt = __shfl_sync(0xffffffffu, v, 0) + NW;
         } else {
-            chunk_span<FX_GLOBAL, U, R, VT, XT>(0, L, off, len, val, c32, c16, seg, x, s);
+            nxt = cur + NW;
         }
-        store(dst, s);
+        const ChunkMeta mn = meta(nxt);
+        XT s[R];
+        if (cur < nv) {
+            // a row too long for one lane: the whole warp
+            const VRow row = vrows[t.vrow0 + cur];
+            warp_row<FXW, U, R, VT, XT>(row, val, c32, c16, seg, x, s);
+            if (lane == 0) store(row.dst, s);
+        } else {
+            // a chunk of 32 rows, one lane per row
+            const int64_t off = (int64_t)mc.off + lane;
+            const int32_t L = __shfl_sync(0xffffffffu, mc.len, 0);   // lane 0 is longest
+#pragma unroll
+            for (int c = 0; c < R; ++c) s[c] = XT(0);
+            if constexpr (KIND == TILE_MIXED) {
+                // rows store their gathered elements first: slots [0, G) may
+                // gather, slots [G, L) read shared memory only
+                chunk_span<FX_MIXED, U, R, VT, XT>(0, mc.mix, off, mc.len, val, c32, c16, seg, x, s);
+                chunk_span<FX_SMEM32, U, R, VT, XT>(mc.mix, L, off, mc.len, val, c32, c16, seg, x, s);
+            } else if constexpr (KIND == TILE_NARROW) {
+                chunk_span<FX_SMEM16, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x, s);
+            } else {
+                chunk_span<FX_GLOBAL, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x, s);
+            }
+            store(mc.dst, s);
+        }
+        cur = nxt;
+        mc = mn;
     }
 }
 
@@ -557,7 +575,8 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
 // mbarrier, `phase` its current parity.
 template <int R, typename VT, typename XT, int NT = kThreads>
 __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> &A,
-                                          uint64_t *bar, uint32_t &phase)
+                                          uint64_t *bar, uint32_t &phase,
+                                          int32_t *claim = nullptr)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     XT *seg = reinterpret_cast<XT *>(smem_raw);
@@ -647,9 +666,9 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
     }
 
     switch (kind) {
-    case TILE_NARROW: rows_work<TILE_NARROW, R, VT, XT, NT>(t, A, seg); break;
-    case TILE_MIXED: rows_work<TILE_MIXED, R, VT, XT, NT>(t, A, seg); break;
-    default: rows_work<TILE_GLOBAL, R, VT, XT, NT>(t, A, seg); break;
+    case TILE_NARROW: rows_work<TILE_NARROW, R, VT, XT, NT>(t, A, seg, claim); break;
+    case TILE_MIXED: rows_work<TILE_MIXED, R, VT, XT, NT>(t, A, seg, claim); break;
+    default: rows_work<TILE_GLOBAL, R, VT, XT, NT>(t, A, seg, claim); break;
     }
     return true;
 }
@@ -664,11 +683,15 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? tile_ctas_per_sm(R)
 k_tiles(const TileArgs<VT, XT> A)
 {
     __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) mbar_init(&bar);
+    __shared__ int32_t claim;          // next item of the tile to hand out
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        claim = 0;
+    }
     __syncthreads();
     uint32_t phase = 0;
     const Tile t = A.tiles[blockIdx.x];
-    tile_work<R, VT, XT, NT>(t, A, &bar, phase);
+    tile_work<R, VT, XT, NT>(t, A, &bar, phase, &claim);
 }
 
 // Persistent CTAs, one per resident slot, claiming tiles in tile order from

@@ -267,6 +267,36 @@ def laplacian3d(n=128, seed=0, permute=True):
     return coo_to_csr(N, N, rows, cols, vals)
 
 
+def weighted_laplacian3d(n=16, seed=0, shift=0.5, permute=True):
+    """Graph Laplacian of the n^3 7-point grid with edge weights U(0.5, 1.5),
+    plus shift on the diagonal: symmetric positive definite, with values that
+    BF16 does not hold exactly.  Symmetrically permuted."""
+    rng = _rng(seed)
+    N = n * n * n
+    idx = np.arange(N, dtype=np.int64)
+    x, y, z = idx % n, (idx // n) % n, idx // (n * n)
+    er, ec, ew = [], [], []
+    for dx, dy, dz in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        ok = (x + dx < n) & (y + dy < n) & (z + dz < n)
+        a = idx[ok]
+        er.append(a)
+        ec.append(a + dx + dy * n + dz * n * n)
+        ew.append(rng.uniform(0.5, 1.5, size=a.size))
+    er, ec, ew = np.concatenate(er), np.concatenate(ec), np.concatenate(ew)
+    diag = np.full(N, float(shift))
+    np.add.at(diag, er, ew)
+    np.add.at(diag, ec, ew)
+    rows = np.concatenate([idx, er, ec])
+    cols = np.concatenate([idx, ec, er])
+    vals = np.concatenate([diag, -ew, -ew])
+    if permute:
+        perm = rng.permutation(N)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(N)
+        rows, cols = inv[rows], inv[cols]
+    return coo_to_csr(N, N, rows, cols, vals)
+
+
 def rmat_batch_specs(count=64, lo=1024, hi=65536, deg_lo=8, deg_hi=32, seed=0):
     """The members of rmat_batch as (scale, degree, seed) triples: row counts
     drawn log-uniformly in [lo, hi] and rounded to a power of two (R-MAT's

@@ -108,3 +108,27 @@ def test_cg_ir_rejects_bad_input(lap):
     other = S.spmv_plan_create(len(rp2) - 1, len(rp2) - 1, rp2, ci2, v2, dtype=0)
     with pytest.raises(S.SpmvError, match="same square matrix"):
         S.spmv_cg_ir(low, other, bd, xd)
+
+
+def test_cg_ir_bf16_values_that_round():
+    """A shifted graph Laplacian with random edge weights: BF16 rounds its
+    values (unlike the 6 / -1 of the plain Laplacian), so the inner products
+    use a perturbed matrix and the FP64 refinement has to make up for it.
+    The FP64 residual still reaches 1e-10 (the oracle's own residual of the
+    returned x agrees), with more refinement steps than FP32 needs."""
+    rp, ci, v = synth.weighted_laplacian3d(16, seed=5)
+    n = len(rp) - 1
+    bf = v.astype(np.float32).view(np.uint32) & 0xFFFF0000
+    assert np.mean(bf.view(np.float32).astype(np.float64) != v) > 0.9
+    b, _ = oracle.spmv(n, n, rp, ci, v, synth.uniform_x(n, 6))
+    bd = torch.from_numpy(b).cuda()
+    f64 = S.spmv_plan_create(n, n, rp, ci, v, dtype=0)
+    outer = {}
+    for dtype in (1, 2):
+        low = S.spmv_plan_create(n, n, rp, ci, v, dtype=dtype)
+        xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = S.spmv_cg_ir(low, f64, bd, xd, tol=1e-10)
+        assert info["converged"] and info["rel_residual"] <= 1e-10, (dtype, info)
+        assert _rel_residual(n, rp, ci, v, b, xd.cpu().numpy()) <= 1.5e-10
+        outer[dtype] = info["outer"]
+    assert outer[2] > outer[1] >= 2, outer
