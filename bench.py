@@ -905,35 +905,42 @@ def precision_solves(S, mat, parts, dev, log):
 # ------------------------------------------------------------- selector --
 def selector_matrix(i):
     """Seeded matrix i of the selector's data: mesh, R-MAT, blocks or Zipf
-    families with 10^4 .. 10^5 rows, taking turns."""
+    families with 10^4 .. 3 x 10^5 rows (log-uniform), taking turns."""
     g = np.random.default_rng(1000 + i)
     fam = i % 4
+    rows = int(np.exp(g.uniform(np.log(1e4), np.log(3e5))))
     if fam == 0:
-        nx = int(g.integers(100, 317))
-        rp, ci, v = synth.mesh5(nx, seed=i)
+        rp, ci, v = synth.mesh5(max(100, int(np.sqrt(rows))), seed=i)
     elif fam == 1:
-        rp, ci, v = synth.rmat(int(g.integers(13, 17)), int(g.integers(4, 17)), seed=i,
-                               chunk=1 << 18)
+        rp, ci, v = synth.rmat(int(np.clip(np.round(np.log2(rows)), 13, 18)),
+                               int(g.integers(4, 17)), seed=i, chunk=1 << 18)
     elif fam == 2:
         nb = int(g.choice([8, 16, 32, 64]))
-        bs = int(g.integers(10000, 50001)) // nb
+        bs = max(256, rows // nb)
         rp, ci, v = synth.blocks(nb, bs, float(g.uniform(8, 24)) / bs, 0.05, seed=i)
     else:
-        m = int(g.integers(10000, 100001))
-        rp, ci, v = synth.zipf_matrix(m, m, seed=i)
+        rp, ci, v = synth.zipf_matrix(rows, rows, seed=i)
     return rp, ci, v
 
 
-def _selector_partitions(i):
+def _selector_partitions(spec):
     """Worker (spawned process, no GPU): the matrix and the partitions its
-    classes need."""
+    classes need (kept in / read from `cache` when given)."""
+    i, cache = spec
     import paper_1203_2739_gb300 as S
     rp, ci, v = selector_matrix(i)
     m = n = len(rp) - 1
     out = {}
     for meth, K in ((S.SPMV_PART_CN, 16), (S.SPMV_PART_CN, 256), (S.SPMV_PART_ERCN, 16),
                     (S.SPMV_PART_ERCN, 256), (S.SPMV_PART_RCN, 256)):
+        path = os.path.join(cache, "sel%d_m%d_K%d.npz" % (i, meth, K)) if cache else None
+        if path and os.path.exists(path):
+            out[(meth, K)] = load_partition(S, path, m, n, rp, ci)
+            continue
         out[(meth, K)] = S.spmv_partition(m, n, rp, ci, meth, K=K, seed=0, threads=1)
+        if path:
+            os.makedirs(cache, exist_ok=True)
+            save_partition(path, out[(meth, K)])
     return i, out
 
 
@@ -958,10 +965,13 @@ def run_selector(args, pool_results):
         feats.append(S.spmv_features(m, n, rp, ci))
         x = torch.from_numpy(synth.uniform_x(n, 1)).to(dev)
         y = torch.empty(m, dtype=torch.float64, device=dev)
-        row = []
-        for fw, K, ct in SEL.CLASSES:
+
+        def build(cls):
+            fw, K, ct = cls
             if fw == "natural":
                 kw = {}
+            elif fw == "tiled":
+                kw = dict(flags=S.SPMV_FLAG_TILED_NATURAL, warp_rows=128)
             elif fw in ("sb", "db"):
                 r = parts[(S.SPMV_PART_CN if fw == "sb" else S.SPMV_PART_ERCN, K)]
                 kw = dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"],
@@ -974,19 +984,26 @@ def run_selector(args, pool_results):
                                                                  lab)
                 kw = dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SPLIT, K=K,
                           row_part_ptr=rpp, col_part_ptr=cpp, nz_part=lab, cta_threads=ct)
-            plan = S.spmv_plan_create(m, n, rp, ci, v, **kw)
-            for _ in range(3):
+            return S.spmv_plan_create(m, n, rp, ci, v, **kw)
+
+        # every class's plan built at once on host threads, then timed in
+        # turns (each call after another class's) with the median kept
+        with cf.ThreadPoolExecutor(max_workers=len(SEL.CLASSES)) as ex:
+            plans = list(ex.map(build, SEL.CLASSES))
+        reps = 15
+        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in plans] for _ in range(reps)]
+        for plan in plans:
+            S.spmv_exec(plan, x, y)
+        for r_ in range(reps):
+            for k, plan in enumerate(plans):
+                ev[r_][k][0].record(stream)
                 S.spmv_exec(plan, x, y)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 20
-            a.record(stream)
-            for _ in range(reps):
-                S.spmv_exec(plan, x, y)
-            b.record(stream)
-            torch.cuda.synchronize()
-            row.append(a.elapsed_time(b) / reps)
-            del plan
-        times.append(row)
+                ev[r_][k][1].record(stream)
+        torch.cuda.synchronize()
+        times.append([float(np.median([ev[r_][k][0].elapsed_time(ev[r_][k][1])
+                                       for r_ in range(reps)])) for k in range(len(plans))])
+        del plans
         nbytes.append(compulsory_bytes(m, n, int(rp[-1])))
         if i % 16 == 15:
             log("  selector data: %d/%d matrices timed" % (i + 1, N))
@@ -999,9 +1016,7 @@ def run_selector(args, pool_results):
     hist = sel.fit(F[:ntr], best[:ntr], epochs=400, lr=3e-3, batch=32)
     train_s = time.perf_counter() - t0
     test = np.arange(ntr, N)
-    p = sel.proba(F[test])
-    pick = p.argmax(axis=1)
-    conf = p.max(axis=1)
+    pick, conf = sel.predict(F[test])
     regret = T[test, pick] / T[test, best[test]] - 1.0
     # fallback: below the confidence threshold, time every class (regret 0)
     thr = 0.5
@@ -1017,8 +1032,9 @@ def run_selector(args, pool_results):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "learned selector: %d seeded matrices (mesh / R-MAT / blocks / "
-                               "Zipf, 1e4-1e5 rows), %d classes (plain CSR; SB, DB, split at "
-                               "K = 16, 256; 256- or 1024-thread tiles); trained on %d, "
+                               "Zipf, 1e4-3e5 rows), %d classes (plain CSR; natural order through "
+                               "the tiled kernel; SB, DB, split at K = 16, 256; 256- or "
+                               "1024-thread tiles); trained on %d, "
                                "evaluated on %d" % (N, len(SEL.CLASSES), ntr, N - ntr),
                    "l2": "matrices smaller than L2: repeated products with L2 warm"},
         "selector": {
@@ -1047,7 +1063,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=sorted(MATRICES) + ["selector"])
-    ap.add_argument("--selector-matrices", type=int, default=96)
+    ap.add_argument("--selector-matrices", type=int, default=200)
     ap.add_argument("--scale-nx", type=int, default=6144,
                     help="grid side of the scale workload's mesh (x exceeds L2 from about 4096)")
     ap.add_argument("--forms", default="")
@@ -1099,7 +1115,9 @@ def main():
         import multiprocessing as mp
         ctx = mp.get_context("spawn")
         with ctx.Pool(max(1, (os.cpu_count() or 4))) as pool:
-            res = dict(pool.map(_selector_partitions, range(args.selector_matrices)))
+            res = dict(pool.map(_selector_partitions,
+                                [(i, args.partition_cache) for i in range(args.selector_matrices)],
+                                chunksize=1))
         run_selector(args, [res[i] for i in range(args.selector_matrices)])
         return
     if args.impl == "reference":

@@ -310,6 +310,18 @@ size_t spmv_mlp_work_bytes(int32_t nh, int32_t nc, int32_t batch);
 spmv_status spmv_mlp_forward(const spmv_mlp *net, const float *X, int32_t batch,
                              float *logits, void *work, void *stream);
 
+/* Predicted class (largest score, the lower class on ties) and its softmax
+ * probability for each of `batch` feature rows: cls[batch] (int32) and
+ * conf[batch] (float), device arrays; work as spmv_mlp_forward.  Async. */
+spmv_status spmv_mlp_predict(const spmv_mlp *net, const float *X, int32_t batch,
+                             int32_t *cls, float *conf, void *work, void *stream);
+
+/* Fold a feature standardisation x' = (x - mu) / sd into the first layer, so
+ * that the network reads unscaled features: W1[o][i] /= sd[i], then
+ * b1[o] -= sum_i W1[o][i] mu[i].  mu, sd: nin device floats.  Async. */
+spmv_status spmv_mlp_fold_scaling(const spmv_mlp *net, const float *mu, const float *sd,
+                                  void *stream);
+
 /* Mean softmax cross-entropy over the batch of labels[b] in [0, nc) (a
  * label outside that range makes *loss NaN and contributes no gradient):
  * *loss (one device float) and its gradient with

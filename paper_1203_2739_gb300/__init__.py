@@ -52,7 +52,8 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_last_error", "spmv_csr_exec_noalloc", "spmv_plan_autotune",
            "spmv_plan_check", "spmv_cg_ir", "spmv_plan_create_batched", "spmv_features",
            "spmv_mlp_param_count", "spmv_mlp_work_bytes", "spmv_mlp_forward", "spmv_mlp_grad",
-           "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder")
+           "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder", "spmv_mlp_predict",
+           "spmv_mlp_fold_scaling")
 SPMV_EMULATE_STATS = 13
 EMULATE_STATS = ("tiles", "chunk_tiles", "staged_tiles", "partial_slots", "fixups", "warp_rows",
                  "stored_chunk_elements", "plain_csr", "gathered_nnz", "fma_lanes",
@@ -163,6 +164,8 @@ def _load():
     L.spmv_mlp_work_bytes.restype = ctypes.c_size_t
     L.spmv_mlp_forward.argtypes = [ctypes.POINTER(spmv_mlp), vp, ctypes.c_int32, vp, vp, vp]
     L.spmv_mlp_grad.argtypes = [ctypes.POINTER(spmv_mlp), vp, vp, ctypes.c_int32, vp, vp, vp, vp]
+    L.spmv_mlp_predict.argtypes = [ctypes.POINTER(spmv_mlp), vp, ctypes.c_int32, vp, vp, vp, vp]
+    L.spmv_mlp_fold_scaling.argtypes = [ctypes.POINTER(spmv_mlp), vp, vp, vp]
     L.spmv_mlp_adam.argtypes = [ctypes.POINTER(spmv_mlp), vp, vp, vp, ctypes.c_int32,
                                 ctypes.c_float, vp]
     L.spmv_plan_create_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(spmv_csr),
@@ -198,7 +201,8 @@ def _load():
                  "spmv_form_from_labels", "spmv_partition", "spmv_csr_exec_noalloc",
                  "spmv_plan_autotune", "spmv_plan_check", "spmv_cg_ir",
                  "spmv_plan_create_batched", "spmv_features", "spmv_mlp_forward",
-                 "spmv_mlp_grad", "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder"):
+                 "spmv_mlp_grad", "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder",
+                 "spmv_mlp_predict", "spmv_mlp_fold_scaling"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -497,6 +501,24 @@ def _net(params, nin, nh, nc):
         raise ValueError("params must be a contiguous CUDA float32 tensor of "
                          "spmv_mlp_param_count(nin, nh, nc) entries")
     return spmv_mlp(nin, nh, nc, params.data_ptr())
+
+
+def spmv_mlp_predict(params, nin, nh, nc, X, cls, conf, work, stream=None):
+    """cls (int32) and conf (float32) per row of X: the network's class and
+    its softmax probability, computed by the library's kernels."""
+    net = _net(params, nin, nh, nc)
+    vp = ctypes.c_void_p
+    _check(lib.spmv_mlp_predict(ctypes.byref(net), vp(X.data_ptr()), X.shape[0],
+                                vp(cls.data_ptr()), vp(conf.data_ptr()), vp(work.data_ptr()),
+                                vp(_stream_handle(stream))))
+
+
+def spmv_mlp_fold_scaling(params, nin, nh, nc, mu, sd, stream=None):
+    """Fold (x - mu) / sd into the first layer (device float32 tensors)."""
+    net = _net(params, nin, nh, nc)
+    vp = ctypes.c_void_p
+    _check(lib.spmv_mlp_fold_scaling(ctypes.byref(net), vp(mu.data_ptr()), vp(sd.data_ptr()),
+                                     vp(_stream_handle(stream))))
 
 
 def spmv_mlp_forward(params, nin, nh, nc, X, logits, work, stream=None):

@@ -160,6 +160,40 @@ spmv_status launch_status(const char *what)
     return SPMV_OK;
 }
 
+// W1[o][i] <- W1[o][i] / sd[i]; b1[o] <- b1[o] - sum_i W1[o][i] mu[i] (new
+// W1, i in order): the first layer then reads unscaled features
+__global__ void k_fold_scaling(float *__restrict__ W1, float *__restrict__ b1,
+                               const float *__restrict__ mu, const float *__restrict__ sd,
+                               int32_t nin, int32_t nh)
+{
+    const int32_t o = blockIdx.x * kT + threadIdx.x;
+    if (o >= nh) return;
+    float acc = b1[o];
+    for (int32_t i = 0; i < nin; ++i) {
+        const float w = W1[(int64_t)o * nin + i] / sd[i];
+        W1[(int64_t)o * nin + i] = w;
+        acc = fmaf(-w, mu[i], acc);
+    }
+    b1[o] = acc;
+}
+
+// per sample: the class of the largest score (the lower class on ties) and
+// its softmax probability, 1 / sum_k exp(z_k - z_max)
+__global__ void k_predict(const float *__restrict__ Z, int32_t batch, int32_t nc,
+                          int32_t *__restrict__ cls, float *__restrict__ conf)
+{
+    const int32_t b = blockIdx.x * kT + threadIdx.x;
+    if (b >= batch) return;
+    const float *z = Z + (int64_t)b * nc;
+    int32_t best = 0;
+    for (int32_t k = 1; k < nc; ++k)
+        if (z[k] > z[best]) best = k;
+    float sum = 0.0f;
+    for (int32_t k = 0; k < nc; ++k) sum += expf(z[k] - z[best]);
+    cls[b] = best;
+    conf[b] = 1.0f / sum;
+}
+
 }  // namespace
 
 extern "C" int64_t spmv_mlp_param_count(int32_t nin, int32_t nh, int32_t nc)
@@ -195,6 +229,43 @@ extern "C" spmv_status spmv_mlp_forward(const spmv_mlp *net, const float *X, int
     k_dense<<<blocks_for((int64_t)batch * net->nc), kT, 0, s>>>(h2, P + L.w3, P + L.b3, logits,
                                                                 batch, net->nh, net->nc, false);
     return launch_status("MLP forward");
+}
+
+extern "C" spmv_status spmv_mlp_predict(const spmv_mlp *net, const float *X, int32_t batch,
+                                        int32_t *cls, float *conf, void *work, void *stream)
+{
+    clear_error();
+    spmv_status st = check_net(net);
+    if (st != SPMV_OK) return st;
+    if (batch < 0 || (batch > 0 && (!X || !cls || !conf || !work))) {
+        set_error("NULL input, output or workspace");
+        return SPMV_E_INVALID;
+    }
+    if (batch == 0) return SPMV_OK;
+    // the logits go to the workspace after the two hidden layers
+    float *z = static_cast<float *>(work) + 2 * (size_t)batch * net->nh;
+    void *hw = work;
+    st = spmv_mlp_forward(net, X, batch, z, hw, stream);
+    if (st != SPMV_OK) return st;
+    k_predict<<<blocks_for(batch), kT, 0, static_cast<cudaStream_t>(stream)>>>(z, batch, net->nc,
+                                                                               cls, conf);
+    return launch_status("MLP prediction");
+}
+
+extern "C" spmv_status spmv_mlp_fold_scaling(const spmv_mlp *net, const float *mu,
+                                             const float *sd, void *stream)
+{
+    clear_error();
+    spmv_status st = check_net(net);
+    if (st != SPMV_OK) return st;
+    if (!mu || !sd) {
+        set_error("NULL feature means or deviations");
+        return SPMV_E_INVALID;
+    }
+    const Layout L = layout(net->nin, net->nh, net->nc);
+    k_fold_scaling<<<blocks_for(net->nh), kT, 0, static_cast<cudaStream_t>(stream)>>>(
+        net->params + L.w1, net->params + L.b1, mu, sd, net->nin, net->nh);
+    return launch_status("feature scaling fold");
 }
 
 extern "C" spmv_status spmv_mlp_grad(const spmv_mlp *net, const float *X, const int32_t *labels,

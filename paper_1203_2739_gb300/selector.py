@@ -10,12 +10,13 @@ This module orchestrates those calls; every operation on the network runs in
 the library's CUDA kernels."""
 import numpy as np
 
-from . import (SPMV_SEL_FEATURES, spmv_features, spmv_mlp_adam, spmv_mlp_forward,
-               spmv_mlp_grad, spmv_mlp_param_count, spmv_mlp_work_bytes)
+from . import (SPMV_SEL_FEATURES, spmv_features, spmv_mlp_adam, spmv_mlp_fold_scaling,
+               spmv_mlp_grad, spmv_mlp_param_count, spmv_mlp_predict, spmv_mlp_work_bytes)
 
-# (framework, K, cta_threads): framework "natural" runs the plain CSR kernel
-CLASSES = [("natural", 1, 0)] + [(fw, K, ct) for fw in ("sb", "db", "split")
-                                 for K in (16, 256) for ct in (256, 1024)]
+# (framework, K, cta_threads): framework "natural" runs the plain CSR kernel,
+# "tiled" the natural order through the tiled kernel
+CLASSES = [("natural", 1, 0), ("tiled", 1, 256)] + [
+    (fw, K, ct) for fw in ("sb", "db", "split") for K in (16, 256) for ct in (256, 1024)]
 
 
 def features(m, n, rowptr, colidx):
@@ -39,23 +40,23 @@ class Selector:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.step = 0
-        self.mu = np.zeros(self.nin, dtype=np.float32)
-        self.sd = np.ones(self.nin, dtype=np.float32)
         self.device = device
 
     def _x(self, F):
         import torch
-        X = (np.asarray(F, dtype=np.float32) - self.mu) / self.sd
-        return torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.device)
+        X = np.ascontiguousarray(np.atleast_2d(F), dtype=np.float32)
+        return torch.from_numpy(X).to(self.device)
 
     def fit(self, F, labels, epochs=300, lr=3e-3, batch=64, seed=0):
         """Train on features F (N x 16) and class labels (N); returns the
         loss of each epoch (full passes over shuffled mini-batches)."""
         import torch
         F = np.asarray(F, dtype=np.float32)
-        self.mu = F.mean(axis=0)
-        self.sd = F.std(axis=0) + 1e-6
-        X = self._x(F)
+        # training reads standardised features; afterwards the scaling is
+        # folded into the first layer, so that the network reads raw ones
+        mu = F.mean(axis=0).astype(np.float32)
+        sd = (F.std(axis=0) + 1e-6).astype(np.float32)
+        X = self._x((F - mu) / sd)
         y = torch.from_numpy(np.asarray(labels, dtype=np.int32)).to(self.device)
         grads = torch.empty_like(self.params)
         loss = torch.zeros(1, dtype=torch.float32, device=self.device)
@@ -76,22 +77,25 @@ class Selector:
                               self.step, lr)
                 tot += float(loss.item()) * idx.numel()
             hist.append(tot / n)
+        spmv_mlp_fold_scaling(self.params, self.nin, self.nh, self.nc,
+                              torch.from_numpy(mu).to(self.device),
+                              torch.from_numpy(sd).to(self.device))
         return hist
 
-    def proba(self, F):
+    def predict(self, F):
+        """(class, softmax probability of that class) per row of raw
+        features F, from the library's kernels."""
         import torch
-        X = self._x(np.atleast_2d(F))
-        logits = torch.empty(X.shape[0], self.nc, dtype=torch.float32, device=self.device)
+        X = self._x(F)
+        cls = torch.empty(X.shape[0], dtype=torch.int32, device=self.device)
+        conf = torch.empty(X.shape[0], dtype=torch.float32, device=self.device)
         work = torch.empty(spmv_mlp_work_bytes(self.nh, self.nc, X.shape[0]), dtype=torch.uint8,
                            device=self.device)
-        spmv_mlp_forward(self.params, self.nin, self.nh, self.nc, X, logits, work)
-        z = logits.cpu().numpy().astype(np.float64)
-        z = np.exp(z - z.max(axis=1, keepdims=True))
-        return z / z.sum(axis=1, keepdims=True)
+        spmv_mlp_predict(self.params, self.nin, self.nh, self.nc, X, cls, conf, work)
+        return cls.cpu().numpy(), conf.cpu().numpy()
 
     def choose(self, F, min_confidence=0.0):
         """Class index per matrix, or -1 where the top probability is below
         min_confidence (the caller then times every class)."""
-        p = self.proba(F)
-        best = p.argmax(axis=1)
-        return np.where(p.max(axis=1) >= min_confidence, best, -1)
+        cls, conf = self.predict(F)
+        return np.where(conf >= min_confidence, cls, -1)

@@ -95,17 +95,34 @@ def test_training_learns_a_labelled_problem():
     Wt = rng.normal(0, 1, (nc, 16))
     F = rng.normal(0, 1, (4500, 16)).astype(np.float32)
     lab = (F @ Wt.T).argmax(axis=1)
+    # (features far from standardised, so that folding the scaling into the
+    # first layer matters)
+    F = (F * rng.uniform(0.5, 20.0, 16) + rng.uniform(-50, 50, 16)).astype(np.float32)
     sel = SEL.Selector(seed=1)
-    before = (sel.proba(F[4000:]).argmax(axis=1) == lab[4000:]).mean()
+    before = (sel.predict(F[4000:])[0] == lab[4000:]).mean()
     hist = sel.fit(F[:4000], lab[:4000], epochs=40, lr=3e-3, batch=200)
-    after = (sel.proba(F[4000:]).argmax(axis=1) == lab[4000:]).mean()
+    cls, conf = sel.predict(F[4000:])
+    after = (cls == lab[4000:]).mean()
     # (the same training in FP64 on the CPU oracle's gradients reaches 0.90)
     assert hist[-1] < 0.2 * hist[0]
     assert after >= 0.82 and after > before + 0.5
+    # the kernels' class and probability against the oracle's FP64 forward
+    # pass of the trained (folded) network on the raw features
+    nin, nh, nc_ = 16, sel.nh, sel.nc
+    parts = _split(sel.params.cpu().numpy(), nin, nh, nc_)
+    _, logits, _ = oracle.mlp_loss_grad(F[4000:], np.zeros(500, np.int32),
+                                        [p.reshape(sh) for p, sh in zip(parts, (
+                                            (nh, nin), (nh,), (nh, nh), (nh,), (nc_, nh),
+                                            (nc_,)))], grads=False)
+    z = logits - logits.max(axis=1, keepdims=True)
+    p_ref = np.exp(z) / np.exp(z).sum(axis=1, keepdims=True)
+    top2 = np.sort(logits, axis=1)[:, -2:]
+    clear = top2[:, 1] - top2[:, 0] > 1e-3           # no near-tie in FP32
+    assert np.array_equal(cls[clear], logits.argmax(axis=1)[clear])
+    assert np.allclose(conf, p_ref.max(axis=1), rtol=1e-4, atol=1e-5)
     # confidence-gated choice: -1 (time every class) only below the threshold
-    p = sel.proba(F[4000:])
     ch = sel.choose(F[4000:], min_confidence=0.9)
-    assert np.all((ch == -1) == (p.max(axis=1) < 0.9))
+    assert np.all((ch == -1) == (conf < 0.9))
 
 
 def test_out_of_range_label_gives_nan_loss_not_a_fault():
