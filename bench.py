@@ -59,9 +59,25 @@ MATRICES = {
               ("blocks64_0.2pct", lambda: synth.blocks(seed=0))],
     "zipf16k": [("zipf16k", lambda: synth.zipf_matrix(seed=0))],
     "precision": [("laplace3d_128", lambda: synth.laplacian3d(128, seed=0))],
-    "scale": [("mesh5_6144", lambda: synth.mesh5(6144, seed=0))],
+    "scale": [("mesh5_6144", lambda: _mesh_with_points("mesh5_6144", 6144))],
     "batching": [("rmat_batch256", lambda: _batch_matrix("rmat_batch256"))],
 }
+# tile shape per "matrix/form" label taken instead of the autotuner's choice
+# (--shape-map: a bench JSON line's detail, or a {label: shape} object), so
+# that a profiled run launches the kernels a timed run chose
+SHAPE_MAP = {}
+
+# grid point of every row of the meshes generated with their points (the
+# scale workload's SB form is cut from the grid)
+MESH_POINTS = {}
+
+
+def _mesh_with_points(name, nx):
+    rp, ci, v, pts = synth.mesh5(nx, seed=0, return_points=True)
+    MESH_POINTS[name] = (nx, pts)
+    return rp, ci, v
+
+
 # the batching workload: member count, largest member's rows, split K values
 # to partition for, partition cache
 BATCH = {"count": 256, "max_rows": 262144, "K": (16,), "cache": None}
@@ -119,7 +135,8 @@ WORKLOAD_TEXT = {
                 "the tiled kernel vs batched split K=16 (row-column-net bisection of each "
                 "matrix); FP32 with --dtype f32",
     "scale": "L2-exceeding point: 5-pt mesh 6144^2 (37.7M rows, 188.7M nnz, x = 302 MB), "
-             "permuted; natural vs SB K=1024",
+             "permuted; natural (plain CSR and tiled kernel) vs SB K=1024 cut from the grid "
+             "(32 x 32 tiles)",
     "precision": "7-pt Dirichlet Laplacian 128^3, permuted; natural, random, DB K=1024 "
                  "SpMV in the chosen dtype; CG with FP64 iterative refinement to 1e-10 "
                  "with FP64 / FP32 / BF16 inner products",
@@ -129,7 +146,7 @@ WORKLOAD_TEXT = {
 def default_forms(workload):
     return (FORMS_SWEEP if workload == "sweep" else (
         ["natural", "random", "tiled", "db1024"] if workload == "precision"
-        else ["natural", "tiled", "sb1024"] if workload == "scale"
+        else ["natural", "tiled", "sbgrid1024"] if workload == "scale"
         else ["natural", "tiled", "batch_split16"] if workload == "batching"
         else ["natural", "tiled", "sb8", "split16"]))
 
@@ -257,7 +274,7 @@ def batched_split_plan(S, name, K, dtype, threads, nrhs=1):
     return S.spmv_plan_create_batched(mats, nz_parts=nz, K=K, dtype=dtype, nrhs=nrhs)
 
 
-def form_kwargs(S, f, rp, ci, parts, seed=0):
+def form_kwargs(S, f, rp, ci, parts, seed=0, name=None):
     """spmv_plan_create arguments of a form, and the partition it came from."""
     m = n = len(rp) - 1
     if f == "natural" or f.startswith("batch"):
@@ -270,6 +287,17 @@ def form_kwargs(S, f, rp, ci, parts, seed=0):
         if f == "rtiled":
             kw["flags"] = S.SPMV_FLAG_TILED_NATURAL
         return kw, None
+    if f.startswith("sbgrid"):
+        # SB form of a mesh from its grid: K square tiles of grid points (the
+        # planted partition of the column-net model on a mesh)
+        K = int(f[6:])
+        t = int(round(np.sqrt(K)))
+        nx, pts = MESH_POINTS[name]
+        gx, gy = pts % nx, pts // nx
+        lab = ((gy * t // nx) * t + gx * t // nx).astype(np.int32)
+        rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SB, t * t, lab)
+        return dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SB, K=t * t, row_part_ptr=rpp,
+                    col_part_ptr=cpp), None
     if f in ("bfs", "rcm") or f.startswith("rn"):
         # the comparison orders of Sec. 5.1, natural form through the tiled
         # kernel
@@ -414,7 +442,7 @@ def kernel_name(info, dtype):
     r = info["nrhs"]
     if info["n_tiles"] == 0:
         return "k_csr_vector<%d, %d, %s, %s>" % (info["lanes"], r, vt, xt)
-    nt = 1024 if info.get("cta_threads", 256) == 1024 else 256
+    nt = info.get("cta_threads", 256) or 256
     return "k_tiles<%d, %s, %s, %d>" % (r, vt, xt, nt)
 
 
@@ -610,7 +638,7 @@ def run_ours(args, rank, world, local_rank):
         y_ref, absax = library_reference(S, m, n, rp, ci, v, x64)
         xt = x64.to(dtype=tdt)
         for f in forms:
-            kw, pres = form_kwargs(S, f, rp, ci, parts)
+            kw, pres = form_kwargs(S, f, rp, ci, parts, name=name)
             t1 = time.perf_counter()
             chosen = None
             shapes = tile_shapes(S, dtype, r, int(rp[-1]))
@@ -623,9 +651,10 @@ def run_ours(args, rank, world, local_rank):
                 # kernel) join each shape's
                 fl = kw.pop("flags", 0)
                 shapes = {k: dict(c, flags=c.get("flags", 0) | fl) for k, c in shapes.items()}
-                if args.shape:
-                    plan = S.spmv_plan_create(m, n, rp, ci, v, **shapes[args.shape], **kw)
-                    chosen = args.shape
+                fixed = args.shape or SHAPE_MAP.get("%s/%s" % (name, f))
+                if fixed:
+                    plan = S.spmv_plan_create(m, n, rp, ci, v, **shapes[fixed], **kw)
+                    chosen = fixed
                 else:
                     names = list(shapes)
                     plan, ibest, _ = S.spmv_plan_autotune(m, n, rp, ci, v,
@@ -1077,6 +1106,9 @@ def main():
     ap.add_argument("--shape", default="", choices=["", "cta256", "cta256w", "cta512", "cta1024",
                                                     "cta256x8"],
                     help="tiled forms with this tile shape instead of the autotuned one")
+    ap.add_argument("--shape-map", default=None,
+                    help="JSON file: a bench line (its detail's tile_shape per plan) or a "
+                         "{matrix/form: shape} object; those plans skip the autotuner")
     ap.add_argument("--partition-cache", default=None,
                     help="directory to keep and reuse host partitions (untimed preprocessing)")
     ap.add_argument("--nrhs", type=int, default=1, choices=[1, 2, 4, 8],
@@ -1086,6 +1118,12 @@ def main():
     ap.add_argument("--batch-max-rows", type=int, default=262144,
                     help="largest member of the batching workload (rows, log-uniform from 1024)")
     args = ap.parse_args()
+    if args.shape_map:
+        with open(args.shape_map) as fh:
+            d = json.loads(fh.read().strip().splitlines()[-1])
+        if "detail" in d:
+            d = {k: e["tile_shape"] for k, e in d["detail"].items() if e.get("tile_shape")}
+        SHAPE_MAP.update(d)
     if args.workload == "batching":
         name = "rmat_batch%d" % args.batch_count
         BATCH.update(count=args.batch_count, max_rows=args.batch_max_rows,
@@ -1099,7 +1137,7 @@ def main():
             "262144]", "%d]" % args.batch_max_rows)
     if args.scale_nx != 6144:
         nx = args.scale_nx
-        MATRICES["scale"] = [("mesh5_%d" % nx, lambda: synth.mesh5(nx, seed=0))]
+        MATRICES["scale"] = [("mesh5_%d" % nx, lambda: _mesh_with_points("mesh5_%d" % nx, nx))]
         WORKLOAD_TEXT["scale"] = WORKLOAD_TEXT["scale"].replace(
             "mesh 6144^2 (37.7M rows, 188.7M nnz, x = 302 MB)", "mesh %d^2" % nx)
     world = int(os.environ.get("WORLD_SIZE", "1"))

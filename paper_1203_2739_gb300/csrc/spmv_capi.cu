@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "spmv_plan_obj.h"
@@ -563,14 +565,36 @@ extern "C" spmv_status spmv_plan_autotune(const spmv_csr *A, const spmv_perm *pe
     // robin over the candidates (each call finds the caches as the previous
     // candidate left them, as in a sequence of different products) and each
     // candidate is judged by its median call
-    for (int32_t i = 0; i < n_candidates; ++i) {
-        spmv_plan *p = nullptr;
-        st = spmv_plan_create(A, perm, splits, &candidates[i], &p);
-        if (st != SPMV_OK) {
-            cleanup(-1);
-            return st;
-        }
-        plans.push_back(p);
+    // the candidates are built on host threads at once (each thread on the
+    // caller's device); the first failure, in candidate order, is reported
+    {
+        int dev = 0;
+        cudaError_t de = cudaGetDevice(&dev);
+        if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+        std::vector<spmv_plan *> built((size_t)n_candidates, nullptr);
+        std::vector<spmv_status> sts((size_t)n_candidates, SPMV_OK);
+        std::vector<std::string> msgs((size_t)n_candidates);
+        std::vector<std::thread> ts;
+        for (int32_t i = 0; i < n_candidates; ++i)
+            ts.emplace_back([&, i]() {
+                cudaError_t e2 = cudaSetDevice(dev);
+                if (e2 != cudaSuccess) {
+                    sts[(size_t)i] = SPMV_E_CUDA;
+                    msgs[(size_t)i] = cudaGetErrorString(e2);
+                    return;
+                }
+                sts[(size_t)i] = spmv_plan_create(A, perm, splits, &candidates[i], &built[(size_t)i]);
+                if (sts[(size_t)i] != SPMV_OK) msgs[(size_t)i] = spmv_last_error();
+            });
+        for (auto &t : ts) t.join();
+        for (int32_t i = 0; i < n_candidates; ++i)
+            if (built[(size_t)i]) plans.push_back(built[(size_t)i]);
+        for (int32_t i = 0; i < n_candidates; ++i)
+            if (sts[(size_t)i] != SPMV_OK) {
+                cleanup(-1);
+                set_error("candidate %d: %s", i, msgs[(size_t)i].c_str());
+                return sts[(size_t)i];
+            }
     }
     size_t xbytes = 0, ybytes = 0;
     for (int32_t j = 0; j < n_candidates; ++j) {

@@ -26,6 +26,8 @@ def test_kernel_names_follow_the_plan():
     assert bench.kernel_name(info, "bf16") == "k_tiles<8, __nv_bfloat16, float, 1024>"
     info["cta_threads"] = 256
     assert bench.kernel_name(info, "f32") == "k_tiles<8, float, float, 256>"
+    info["cta_threads"] = 512
+    assert bench.kernel_name(info, "f64") == "k_tiles<8, double, double, 512>"
 
 
 def test_partition_cache_round_trip(tmp_path):
