@@ -67,6 +67,20 @@ MATRICES = {
 # that a profiled run launches the kernels a timed run chose
 SHAPE_MAP = {}
 
+def load_shape_map(path):
+    """{matrix/form: tile shape} from a JSON object of that form or from a
+    bench run's output (its last line's detail)."""
+    with open(path) as fh:
+        text = fh.read().strip()
+    try:
+        d = json.loads(text)
+    except ValueError:
+        d = json.loads(text.splitlines()[-1])
+    if "detail" in d:
+        d = {k: e["tile_shape"] for k, e in d["detail"].items() if e.get("tile_shape")}
+    return d
+
+
 # grid point of every row of the meshes generated with their points (the
 # scale workload's SB form is cut from the grid)
 MESH_POINTS = {}
@@ -190,6 +204,8 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     m = n = len(rp) - 1
     need = {}
     for f in forms:
+        if f.startswith("sbgrid"):
+            continue                    # cut from the mesh's grid, no bisection
         if f.startswith("sb"):
             need[("cn", int(f[2:]))] = (S.SPMV_PART_CN, int(f[2:]))
         elif f.startswith("db"):
@@ -1119,11 +1135,7 @@ def main():
                     help="largest member of the batching workload (rows, log-uniform from 1024)")
     args = ap.parse_args()
     if args.shape_map:
-        with open(args.shape_map) as fh:
-            d = json.loads(fh.read().strip().splitlines()[-1])
-        if "detail" in d:
-            d = {k: e["tile_shape"] for k, e in d["detail"].items() if e.get("tile_shape")}
-        SHAPE_MAP.update(d)
+        SHAPE_MAP.update(load_shape_map(args.shape_map))
     if args.workload == "batching":
         name = "rmat_batch%d" % args.batch_count
         BATCH.update(count=args.batch_count, max_rows=args.batch_max_rows,

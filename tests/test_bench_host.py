@@ -1,6 +1,7 @@
 """Host logic of bench.py: the compulsory-bytes unit, kernel naming for the
 dominant-kernel roofline, the partition cache round trip and the split
 forms cut from one recursion tree."""
+import json
 import os
 
 import numpy as np
@@ -279,3 +280,13 @@ def test_err_ratio_flags_unwritten_entries():
     assert bench.err_ratio([1.0, 2.0], [1.0, 2.5], [1.0, 1.0]) == 0.5
     with pytest.raises(RuntimeError):
         bench.err_ratio([float("nan")], [0.0], [1.0])
+
+
+def test_shape_map_from_object_or_bench_line(tmp_path):
+    obj = tmp_path / "m.json"
+    obj.write_text('{\n "a/sb1024": "cta256w",\n "b/tiled": "cta512"\n}\n')
+    assert bench.load_shape_map(str(obj)) == {"a/sb1024": "cta256w", "b/tiled": "cta512"}
+    line = tmp_path / "b.json"
+    line.write_text("log line\n" + json.dumps({"detail": {
+        "a/sb1024": {"tile_shape": "cta1024"}, "a/natural": {"tile_shape": None}}}) + "\n")
+    assert bench.load_shape_map(str(line)) == {"a/sb1024": "cta1024"}
