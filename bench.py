@@ -50,8 +50,8 @@ import synth  # noqa: E402
 # natural and random orders run through both the plain CSR kernel and the
 # tiled kernel ("tiled", "rtiled"), so that the gain of a reordering is
 # measured against the same kernel in the original order
-FORMS_SWEEP = ["natural", "random", "tiled", "rtiled", "bfs", "rcm", "rn1024", "sb1024", "db1024",
-               "split4", "split16", "split64", "split256"]
+FORMS_SWEEP = ["natural", "random", "tiled", "rtiled", "bfs", "rcm", "rn1024", "sb1024", "sbfit96",
+               "db1024", "split4", "split16", "split64", "split256"]
 NATURAL_FORMS = ("natural", "random", "tiled", "rtiled")
 MATRICES = {
     "sweep": [("mesh5_1024", lambda: synth.mesh5(1024, seed=0)),
@@ -141,7 +141,8 @@ def _batch_matrix(name):
 WORKLOAD_TEXT = {
     "sweep": "FP64 reordering sweep: mesh 1024^2 (5-pt, permuted), R-MAT 2^20 deg 16, "
              "64 blocks of 16384^2 at 0.2% + 5% border (shuffled); natural, random (plain CSR "
-             "and tiled kernel), sBFS, sRCM, sHP_RN K=1024, SB K=1024, DB K=1024, "
+             "and tiled kernel), sBFS, sRCM, sHP_RN K=1024, SB K=1024, SB by the fit rule "
+             "(x subvector of each part < 96 KB), DB K=1024, "
              "split K=4/16/64/256",
     "zipf16k": "Zipf 16384^2 (rows P(d)~d^-1.7498 on [1,512], Zipf(1.2) columns), natural vs SB",
     "batching": "256 R-MAT matrices (rows log-uniform in [1024, 262144], power-of-two sizes, "
@@ -206,14 +207,20 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     for f in forms:
         if f.startswith("sbgrid"):
             continue                    # cut from the mesh's grid, no bisection
-        if f.startswith("sb"):
-            need[("cn", int(f[2:]))] = (S.SPMV_PART_CN, int(f[2:]))
+        if f.startswith("sbfit"):
+            # the paper's stop rule (Sec. 5.1) on the GPU's window: bisect
+            # until each part's x subvector is below `kb` KB (SPMV_FIT_X)
+            kb = int(f[5:])
+            need[("cnfit", kb)] = dict(method=S.SPMV_PART_CN, K=0, part_bytes=kb * 1024,
+                                       fit_rule=S.SPMV_FIT_X)
+        elif f.startswith("sb"):
+            need[("cn", int(f[2:]))] = dict(method=S.SPMV_PART_CN, K=int(f[2:]))
         elif f.startswith("db"):
-            need[("ercn", int(f[2:]))] = (S.SPMV_PART_ERCN, int(f[2:]))
+            need[("ercn", int(f[2:]))] = dict(method=S.SPMV_PART_ERCN, K=int(f[2:]))
         elif f.startswith("split"):
-            need[("rcn", 256)] = (S.SPMV_PART_RCN, 256)
+            need[("rcn", 256)] = dict(method=S.SPMV_PART_RCN, K=256)
         elif f.startswith("rn"):
-            need[("rn", int(f[2:]))] = (S.SPMV_PART_RN, int(f[2:]))
+            need[("rn", int(f[2:]))] = dict(method=S.SPMV_PART_RN, K=int(f[2:]))
     res = {}
     # the breadth-first orders (sBFS, sRCM) take seconds: not cached
     for f in forms:
@@ -235,9 +242,8 @@ def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     if not need:
         return res
     with cf.ThreadPoolExecutor(max_workers=len(need)) as ex:
-        futs = {key: ex.submit(S.spmv_partition, m, n, rp, ci, meth, K=K, seed=seed,
-                               threads=threads)
-                for key, (meth, K) in need.items()}
+        futs = {key: ex.submit(S.spmv_partition, m, n, rp, ci, seed=seed, threads=threads, **kw)
+                for key, kw in need.items()}
         for key, fu in futs.items():
             res[key] = fu.result()
             if cache_dir:
@@ -320,6 +326,10 @@ def form_kwargs(S, f, rp, ci, parts, seed=0, name=None):
         r = parts[(f, 0) if f in ("bfs", "rcm") else ("rn", int(f[2:]))]
         return dict(row_perm=r["row_perm"], col_perm=r["col_perm"],
                     flags=S.SPMV_FLAG_TILED_NATURAL), r
+    if f.startswith("sbfit"):
+        r = parts[("cnfit", int(f[5:]))]
+        return dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"], K=r["K"],
+                    row_part_ptr=r["row_part_ptr"], col_part_ptr=r["col_part_ptr"]), r
     if f.startswith("sb") or f.startswith("db"):
         r = parts[("cn" if f.startswith("sb") else "ercn", int(f[2:]))]
         return dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"], K=r["K"],

@@ -3,7 +3,8 @@
 The FP64 sweep's three 1,048,576-row matrices (5-point mesh 1024^2, R-MAT
 degree 16, 64 blocks of 16384^2 with a 5% border) are ordered and bisected
 exactly as bench.py does (sBFS, sRCM, row-net K = 1024 for sHP_RN,
-column-net K = 1024 for SB, enhanced row-column-net K = 1024 for DB,
+column-net K = 1024 and column-net until each part's x subvector is below
+96 KB for SB, enhanced row-column-net K = 1024 for DB,
 row-column-net K = 256 cut into the K = 4 / 16 / 64 / 256 splits),
 and every tiled form of the sweep is built in every tile shape the
 autotuner chooses from -- so whichever shape it keeps has been checked --
@@ -31,8 +32,8 @@ pytestmark = pytest.mark.gpu
 
 S = None
 SWEEP = ("mesh5_1024", "rmat20_d16", "blocks64_0.2pct")
-TILED_FORMS = ["tiled", "rtiled", "bfs", "rcm", "rn1024", "sb1024", "db1024", "split4",
-               "split16", "split64", "split256"]
+TILED_FORMS = ["tiled", "rtiled", "bfs", "rcm", "rn1024", "sb1024", "sbfit96", "db1024",
+               "split4", "split16", "split64", "split256"]
 
 
 @pytest.fixture(scope="module", autouse=True)
