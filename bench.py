@@ -198,15 +198,32 @@ def make_matrices(workload, log=None, only=None):
 
 
 # ---------------------------------------------------------------- forms --
+ICSR = "_icsr"
+
+
+def base_form(f):
+    """A form name without its storage suffix: "<form>_icsr" is <form> with
+    the column indices of its unstaged chunks stored as 16-bit increments
+    along each row (SPMV_FLAG_COL_DELTA; ICSR's colDiff, Sec. 2.1)."""
+    return f[:-len(ICSR)] if f.endswith(ICSR) else f
+
+
 def partition_jobs(S, rp, ci, forms, seed, threads, cache_dir=None, name=""):
     """Host partitions every requested form needs, run concurrently.  With
     cache_dir, results are kept there as .npz files keyed by matrix, model,
     K and seed, and reused (preprocessing is not part of the timed step)."""
     m = n = len(rp) - 1
     need = {}
+    forms = [base_form(f) for f in forms]
     for f in forms:
         if f.startswith("sbgrid"):
             continue                    # cut from the mesh's grid, no bisection
+        if f.startswith("sbnest") or f.startswith("dbnest"):
+            # the SB / DB partition, its border in the nested order
+            K = int(f[6:])
+            need[("cn" if f[0] == "s" else "ercn", K)] = dict(
+                method=S.SPMV_PART_CN if f[0] == "s" else S.SPMV_PART_ERCN, K=K)
+            continue
         if f.startswith("sbfit"):
             # the paper's stop rule (Sec. 5.1) on the GPU's window: bisect
             # until each part's x subvector is below `kb` KB (SPMV_FIT_X)
@@ -298,6 +315,13 @@ def batched_split_plan(S, name, K, dtype, threads, nrhs=1):
 
 def form_kwargs(S, f, rp, ci, parts, seed=0, name=None):
     """spmv_plan_create arguments of a form, and the partition it came from."""
+    if f.endswith(ICSR):
+        b = base_form(f)
+        if b in ("natural", "random") or b.startswith("batch"):
+            raise ValueError("%s: the plain CSR kernel has no increment storage" % f)
+        kw, pres = form_kwargs(S, b, rp, ci, parts, seed, name)
+        kw["flags"] = kw.get("flags", 0) | S.SPMV_FLAG_COL_DELTA
+        return kw, pres
     m = n = len(rp) - 1
     if f == "natural" or f.startswith("batch"):
         return {}, None
@@ -326,6 +350,15 @@ def form_kwargs(S, f, rp, ci, parts, seed=0, name=None):
         r = parts[(f, 0) if f in ("bfs", "rcm") else ("rn", int(f[2:]))]
         return dict(row_perm=r["row_perm"], col_perm=r["col_perm"],
                     flags=S.SPMV_FLAG_TILED_NATURAL), r
+    if f.startswith("sbnest") or f.startswith("dbnest"):
+        # SB / DB with each bisection's cut columns between its halves
+        # (SPMV_ORDER_NESTED), natural form through the tiled kernel
+        r = parts[("cn" if f[0] == "s" else "ercn", int(f[6:]))]
+        if "nested" not in r:
+            r["nested"] = S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, int(r["K"]),
+                                         r["labels"])
+        rperm, cperm = r["nested"]
+        return dict(row_perm=rperm, col_perm=cperm, flags=S.SPMV_FLAG_TILED_NATURAL), r
     if f.startswith("sbfit"):
         r = parts[("cnfit", int(f[5:]))]
         return dict(row_perm=r["row_perm"], col_perm=r["col_perm"], form=r["form"], K=r["K"],
@@ -881,6 +914,10 @@ def reorder_gains(detail):
             # order's, with the same kernel (lower is better)
             e["normalized_time"] = {f: round(t / us["tiled"], 3) for f, t in us.items()
                                     if f not in ("natural", "random", "tiled")}
+        # 16-bit column increments against 32-bit indices, same form
+        inc = {f: round(us[f] / us[f + ICSR], 3) for f in us if f + ICSR in us}
+        if inc:
+            e["icsr_gain"] = inc
         out[mat] = e
     norm = [e["normalized_time"] for e in out.values() if "normalized_time" in e]
     if norm:

@@ -82,13 +82,22 @@ enum {
     SPMV_FLAG_STAGE = 16,        /* stage x in 256-thread CTAs too; by default
                                     only 512- and 1024-thread CTAs stage, whose
                                     windows are large enough to pay */
-    SPMV_FLAG_TEST_WAIT_EXPIRES = 32  /* tests of failure detection only: the
+    SPMV_FLAG_TEST_WAIT_EXPIRES = 32, /* tests of failure detection only: the
                                     first wait of every staged tile on its
                                     staging copy gives up at once, so every
                                     staged tile is skipped and spmv_plan_check
                                     reports SPMV_E_TIMEOUT (the copy is still
                                     awaited, with the normal bound, before the
                                     CTA exits) */
+    SPMV_FLAG_COL_DELTA = 64     /* tiled forms: the chunks of tiles that stage
+                                    nothing store their column indices as
+                                    16-bit increments along each row from a
+                                    32-bit base column per chunk (the colDiff
+                                    array of ICSR, Sec. 2.1, kept per lane: 2
+                                    bytes per nonzero instead of 4).  A chunk
+                                    with an increment above 65535 keeps 32-bit
+                                    indices.  Rows too long for one lane (the
+                                    warp rows and the chunk tiles) always do */
 };
 
 /* CSR matrix in host memory, caller-owned (Sec. 2.1: nonzero = vals,
@@ -179,6 +188,8 @@ typedef struct spmv_plan_info {
     int64_t moved_bytes;        /* bytes one exec reads/writes if every array
                                    element it touches is moved once */
     int32_t cta_threads;        /* tiled kernel CTA size (0: plain CSR kernel) */
+    int64_t delta_nnz;          /* nonzeros stored as 16-bit column increments
+                                   (SPMV_FLAG_COL_DELTA) */
 } spmv_plan_info;
 
 /* Build a plan: validate A, the permutation and the form (eqs. 1, 2, 5 or
@@ -429,9 +440,10 @@ spmv_status spmv_partition(const spmv_csr *A, const spmv_partition_opts *opts,
                            spmv_partition_out *out);
 void spmv_partition_free(spmv_partition_out *out);
 
-/* Row and column orders of the paper's comparison methods (Sec. 5.1), host
- * only, into caller-allocated row_perm[m] and col_perm[n] (new -> old),
- * for a plan of form SPMV_NATURAL.  The bipartite graph of A has a vertex per
+/* Row and column orders of the paper's comparison methods (Sec. 5.1) and
+ * the nested border order of the SB / DB forms, host only, into
+ * caller-allocated row_perm[m] and col_perm[n] (new -> old), for a plan of
+ * form SPMV_NATURAL (through the tiled kernel: SPMV_FLAG_TILED_NATURAL).  The bipartite graph of A has a vertex per
  * row and per column and an edge per nonzero; ties go to the lower vertex
  * (rows before columns, then by index).
  *   SPMV_ORDER_BFS (sBFS): breadth-first search from row 0, neighbours in
@@ -447,11 +459,22 @@ void spmv_partition_free(spmv_partition_out *out);
  *     subtree first); columns by (label, index); a row whose columns all lie
  *     in leaf k goes to block k, a row whose labels span a..b (a < b) to the
  *     separator of the bisection that split a from b, placed between that
- *     bisection's two halves; empty rows last; ties by index.
+ *     bisection's two halves; empty rows last; ties by index.  labels are
+ *     the n column labels.
+ *   SPMV_ORDER_NESTED (the SB / DB forms with a nested border, Sec. 3.1 and
+ *     3.2): labels[m] in [0, K], K a power of two, are the row parts of an SB
+ *     (CN) or DB (eRCN, label K = the row border R_B) partition, the leaves
+ *     of its recursive bisection (left subtree first).  Rows by (label,
+ *     index), R_B last.  A column whose rows outside R_B all lie in part k
+ *     goes to C_k; a coupling column whose rows span parts a..b (a < b) goes
+ *     to the border of the bisection that split a from b, placed between
+ *     that bisection's two halves (the cut columns of a bisection sit
+ *     between the column slices of its halves instead of in one C_B at the
+ *     end); columns no part touches last; ties by index.
  * Errors: SPMV_E_INVALID (bad CSR, K, labels or method). */
-enum { SPMV_ORDER_BFS = 0, SPMV_ORDER_RCM = 1, SPMV_ORDER_SBD = 2 };
-spmv_status spmv_reorder(const spmv_csr *A, int32_t method, int32_t K,
-                         const int32_t *col_labels, int32_t *row_perm, int32_t *col_perm);
+enum { SPMV_ORDER_BFS = 0, SPMV_ORDER_RCM = 1, SPMV_ORDER_SBD = 2, SPMV_ORDER_NESTED = 3 };
+spmv_status spmv_reorder(const spmv_csr *A, int32_t method, int32_t K, const int32_t *labels,
+                         int32_t *row_perm, int32_t *col_perm);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *spmv_last_error(void);
@@ -507,9 +530,10 @@ spmv_status spmv_csr_exec_noalloc(int32_t m, int32_t n, int64_t nnz,
  * elements (with padding), 1 if the plain CSR kernel is used, nonzeros whose
  * x is gathered (not staged), FMA lanes the tiles issue, element slots that
  * load x from both global and shared memory, x entries staged, tiles that
- * stage a second run.  Errors: those of spmv_plan_create's validation,
+ * stage a second run, nonzeros stored as 16-bit column increments
+ * (SPMV_FLAG_COL_DELTA).  Errors: those of spmv_plan_create's validation,
  * SPMV_E_INTERNAL, SPMV_E_NOMEM. */
-#define SPMV_EMULATE_STATS 13
+#define SPMV_EMULATE_STATS 14
 spmv_status spmv_plan_emulate(const spmv_csr *A, const spmv_perm *perm,
                               const spmv_splits *splits, const spmv_opts *opts,
                               int32_t n_sm, const double *x, double *y, int64_t *stats);

@@ -19,6 +19,13 @@ The bipartite graph of A has a vertex per row (ids 0 .. m-1) and per column
   leaves, K a power of two, left subtree first) in block k; a row whose parts
   span leaves a < b in the separator of the bisection that parted a from b,
   placed between that bisection's halves; empty rows last; ties by index.
+* ``nested_order``  the nested reading of the SB / DB border (the parts of a
+  row-side bisection tree, K leaves, K a power of two, left subtree first;
+  label K marks the DB row border): rows by (part, index), the row border
+  last; a column whose rows outside the row border all lie in part k in
+  column block k; a column whose rows span parts a < b in the border of the
+  bisection that parted a from b, placed between that bisection's halves;
+  columns no part touches last; ties by index.
 """
 from collections import deque
 
@@ -132,4 +139,39 @@ def sbd_order(m, n, rowptr, colidx, K, col_labels):
                 return (2 * mid - 1, i)
 
     rows = sorted(range(m), key=block)
+    return np.array(rows, dtype=np.int32), np.array(cols, dtype=np.int32)
+
+
+def _between(a, b, K):
+    """Key of a block spanning leaves a < b: walk down the bisection tree from
+    the root until a and b fall on different sides; the border of that
+    bisection sits just before its right half's first leaf."""
+    lo, hi = 0, K
+    while True:
+        mid = (lo + hi) // 2
+        if b < mid:
+            hi = mid
+        elif a >= mid:
+            lo = mid
+        else:
+            return 2 * mid - 1
+
+
+def nested_order(m, n, rowptr, colidx, K, row_labels):
+    lab = [int(t) for t in row_labels]
+    rows = sorted(range(m), key=lambda i: (lab[i], i))
+    parts = [[] for _ in range(n)]
+    for i in range(m):
+        if lab[i] == K:
+            continue                      # the DB row border
+        for p in range(int(rowptr[i]), int(rowptr[i + 1])):
+            parts[int(colidx[p])].append(lab[i])
+
+    def block(j):
+        if not parts[j]:
+            return (2 * K, j)
+        a, b = min(parts[j]), max(parts[j])
+        return (2 * a, j) if a == b else (_between(a, b, K), j)
+
+    cols = sorted(range(n), key=block)
     return np.array(rows, dtype=np.int32), np.array(cols, dtype=np.int32)

@@ -36,8 +36,9 @@ SPMV_NATURAL, SPMV_SB, SPMV_DB, SPMV_SPLIT = 0, 1, 2, 3
 SPMV_FLAG_NO_STAGING, SPMV_FLAG_TILED_NATURAL, SPMV_FLAG_SM_AFFINE = 1, 2, 4
 SPMV_FLAG_PERSISTENT, SPMV_FLAG_STAGE = 8, 16
 SPMV_FLAG_TEST_WAIT_EXPIRES = 32
+SPMV_FLAG_COL_DELTA = 64
 SPMV_PART_CN, SPMV_PART_ERCN, SPMV_PART_RCN, SPMV_PART_RANDOM, SPMV_PART_RN = 0, 1, 2, 3, 4
-SPMV_ORDER_BFS, SPMV_ORDER_RCM, SPMV_ORDER_SBD = 0, 1, 2
+SPMV_ORDER_BFS, SPMV_ORDER_RCM, SPMV_ORDER_SBD, SPMV_ORDER_NESTED = 0, 1, 2, 3
 SPMV_FIT_CSR, SPMV_FIT_X = 0, 1
 
 STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_E_INVALID", 2: "SPMV_E_STRUCTURE", 3: "SPMV_E_NOMEM",
@@ -54,10 +55,10 @@ EXPORTS = ("spmv_plan_create", "spmv_exec", "spmv_exec_host", "spmv_permute_x",
            "spmv_mlp_param_count", "spmv_mlp_work_bytes", "spmv_mlp_forward", "spmv_mlp_grad",
            "spmv_mlp_adam", "spmv_plan_emulate", "spmv_reorder", "spmv_mlp_predict",
            "spmv_mlp_fold_scaling")
-SPMV_EMULATE_STATS = 13
+SPMV_EMULATE_STATS = 14
 EMULATE_STATS = ("tiles", "chunk_tiles", "staged_tiles", "partial_slots", "fixups", "warp_rows",
                  "stored_chunk_elements", "plain_csr", "gathered_nnz", "fma_lanes",
-                 "mixed_slots", "staged_entries", "two_run_tiles")
+                 "mixed_slots", "staged_entries", "two_run_tiles", "delta_nnz")
 SPMV_NOALLOC_MAX_NNZ = 1073741824
 
 
@@ -108,7 +109,7 @@ class spmv_plan_info(ctypes.Structure):
                 ("list_entries", ctypes.c_int64), ("partial_slots", ctypes.c_int64),
                 ("fixup_rows", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("compulsory_bytes", ctypes.c_int64), ("moved_bytes", ctypes.c_int64),
-                ("cta_threads", ctypes.c_int32)]
+                ("cta_threads", ctypes.c_int32), ("delta_nnz", ctypes.c_int64)]
 
 
 class spmv_partition_opts(ctypes.Structure):
@@ -622,12 +623,13 @@ def spmv_form_from_labels(m, n, rowptr, colidx, form, K, labels):
     return rperm, cperm, rpp, cpp
 
 
-def spmv_reorder(m, n, rowptr, colidx, method, K=0, col_labels=None):
+def spmv_reorder(m, n, rowptr, colidx, method, K=0, labels=None):
     """Row and column orders of the comparison methods (sBFS, sRCM, and the
-    nested separated block-diagonal order of sHP_RN from column labels):
+    nested separated block-diagonal order of sHP_RN from column labels) and
+    the nested border order of SB / DB forms (from row labels):
     (row_perm, col_perm), new -> old."""
     A, keep = _csr_struct(m, n, rowptr, colidx, None)
-    lab = None if col_labels is None else _i32(col_labels)
+    lab = None if labels is None else _i32(labels)
     rperm = np.empty(m, dtype=np.int32)
     cperm = np.empty(n, dtype=np.int32)
     _check(lib.spmv_reorder(ctypes.byref(A), method, K, _ptr(lab), _ptr(rperm), _ptr(cperm)))

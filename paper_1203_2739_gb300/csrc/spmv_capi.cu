@@ -219,7 +219,8 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         if (!tiled) add_vec(a, hp.rowptr, (const void **)&dp.rowptr);
         add_vec(a, hp.col32, (const void **)&dp.col32);
         a.add(vhost, vbytes, const_cast<void **>(&dp.val));
-        if (tiled && hp.narrow_nnz > 0) add_vec(a, hp.col16, (const void **)&dp.col16);
+        if (tiled && hp.narrow_nnz + hp.delta_nnz > 0)
+            add_vec(a, hp.col16, (const void **)&dp.col16);
         if (!tiled && !hp.long_rows.empty())
             add_vec(a, hp.long_rows, (const void **)&dp.long_rows);
         if (tiled) {
@@ -314,6 +315,7 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
         I.launches_per_exec = hp.m == 0 ? 0 : (tiled ? (dp.n_tiles > 0) + (dp.n_fixups > 0) : 1);
         I.smem_bytes = dp.smem_bytes;
         I.cta_threads = tiled ? hp.cta_threads : 0;
+        I.delta_nnz = hp.delta_nnz;
         I.staged_entries = hp.staged_entries;
         I.list_entries = hp.list_entries;
         I.partial_slots = hp.partial_slots;
@@ -325,8 +327,9 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
             I.moved_bytes = I.compulsory_bytes + (int64_t)dp.n_long * 4;
         } else {
             // every element touched once: values and indices (16-bit in narrow
-            // tiles) of the stored rows, chunk metadata, tiles, staged x (+ list
-            // indices), x read directly (distinct columns), y, partials, fix-ups
+            // tiles and increment chunks) of the stored rows, chunk metadata,
+            // tiles, staged x (+ list indices), x read directly (distinct
+            // columns), y, partials, fix-ups
             std::vector<char> seen((size_t)hp.n, 0);
             int64_t gdistinct = 0;
             auto see = [&](int32_t c) {
@@ -363,7 +366,8 @@ extern "C" spmv_status spmv_plan_create(const spmv_csr *A, const spmv_perm *perm
                         }
                     }
             }
-            I.moved_bytes = hp.nnz * vb + hp.narrow_nnz * 2 + (hp.nnz - hp.narrow_nnz) * 4 +
+            const int64_t short_idx = hp.narrow_nnz + hp.delta_nnz;
+            I.moved_bytes = hp.nnz * vb + short_idx * 2 + (hp.nnz - short_idx) * 4 +
                             (int64_t)hp.slot_dst.size() * 8 + (int64_t)hp.chunk_off.size() * 8 +
                             (int64_t)hp.vrows.size() * 16 +
                             (int64_t)hp.tiles.size() * (int64_t)sizeof(Tile) +

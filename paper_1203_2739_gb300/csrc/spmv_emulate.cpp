@@ -114,6 +114,40 @@ bool run_plain(Emu &E)
     return true;
 }
 
+// A chunk of column increments (DELTA tiles), as the kernel reads it: lane
+// i's running column starts at the base B and adds the increment of every
+// element slot up to the chunk's longest row L, padding included; the kernel
+// gathers x at every such column, so each must lie in [0, n).  Padding adds
+// 0, so a lane's column stays at its row's last one.
+bool run_delta_chunk(Emu &E, int64_t off, int32_t L, int32_t B, int64_t ch)
+{
+    const HostPlan &P = E.P;
+    const int32_t r = E.r;
+    if (off & 1) return E.fail("increment chunk at an odd element", ch, off);
+    if (off + 32 * (int64_t)L > (int64_t)P.col16.size())
+        return E.fail("increment chunk storage", ch, off);
+    std::vector<double> s((size_t)r);
+    for (int32_t i = 0; i < 32; ++i) {
+        const int32_t len = P.slot_len[(size_t)ch * 32 + i];
+        const int32_t dst = P.slot_dst[(size_t)ch * 32 + i];
+        if (len < 0 || len > L) return E.fail("chunk rows not sorted by length", ch, i);
+        if (dst == -1 && len != 0) return E.fail("empty slot with elements", ch, i);
+        int64_t c = B;
+        for (int32_t k = 0; k < r; ++k) s[k] = 0.0;
+        for (int32_t k = 0; k < L; ++k) {
+            const uint16_t d = P.col16[(size_t)delta_pos(off, L, k, i)];
+            if (k >= len && d != 0) return E.fail("padding increment is not 0", ch, k);
+            c += d;
+            if (c >= P.n) return E.fail("running column beyond n", ch, c);
+            if (k >= len) continue;
+            const int64_t e = off + 32 * (int64_t)k + i;
+            for (int32_t q = 0; q < r; ++q) s[q] += P.val[(size_t)e] * E.xh[(size_t)c * r + q];
+        }
+        if (!E.store(dst, s.data())) return false;
+    }
+    return true;
+}
+
 bool run_tile(Emu &E, const Tile &t)
 {
     const HostPlan &P = E.P;
@@ -126,7 +160,8 @@ bool run_tile(Emu &E, const Tile &t)
             return false;
         return E.store(dst_partial(t.slot), s.data());
     }
-    if (t.kind != TILE_NARROW && t.kind != TILE_MIXED && t.kind != TILE_GLOBAL)
+    if (t.kind != TILE_NARROW && t.kind != TILE_MIXED && t.kind != TILE_GLOBAL &&
+        t.kind != TILE_DELTA)
         return E.fail("tile kind", t.kind, 0);
     // the staged window: the first run, the second run (at run2_at), then
     // the gathered list
@@ -173,14 +208,17 @@ bool run_tile(Emu &E, const Tile &t)
         for (int32_t k = 0; k < r; ++k)
             E.win[(size_t)(lat + i) * r + k] = E.xh[(size_t)g * r + k];
     }
-    if (t.kind == TILE_GLOBAL && E.n_win != 0) return E.fail("global tile stages", E.n_win, 0);
+    if ((t.kind == TILE_GLOBAL || t.kind == TILE_DELTA) && E.n_win != 0)
+        return E.fail("unstaged tile stages", E.n_win, 0);
+    // warp rows and col32 chunks of a DELTA tile read x as a GLOBAL tile does
+    const int32_t kind32 = t.kind == TILE_DELTA ? TILE_GLOBAL : t.kind;
     // rows reduced by a warp
     for (int32_t w = 0; w < t.nvrows; ++w) {
         const int64_t vi = (int64_t)t.vrow0 + w;
         if (vi < 0 || vi >= (int64_t)P.vrows.size()) return E.fail("warp row", vi, 0);
         const VRow v = P.vrows[(size_t)vi];
         if (v.len < 0) return E.fail("warp row length", vi, v.len);
-        if (!E.row_sum(t.kind, [&v](int32_t j) { return (int64_t)v.e0 + j; }, v.len, s.data()))
+        if (!E.row_sum(kind32, [&v](int32_t j) { return (int64_t)v.e0 + j; }, v.len, s.data()))
             return false;
         if (!E.store(v.dst, s.data())) return false;
     }
@@ -198,8 +236,13 @@ bool run_tile(Emu &E, const Tile &t)
             return E.fail("chunk storage", ch, off);
         if (ch >= (int64_t)P.chunk_mix.size()) return E.fail("chunk mix prefix", ch, 0);
         const int32_t G = P.chunk_mix[(size_t)ch];
-        if (G < 0 || G > longest || (t.kind != TILE_MIXED && G != 0))
+        if (t.kind == TILE_DELTA) {
+            if (G < -1 || G >= P.n) return E.fail("chunk base column", ch, G);
+            if (G >= 0 && !run_delta_chunk(E, off, longest, G, ch)) return false;
+            if (G >= 0) continue;
+        } else if (G < 0 || G > longest || (t.kind != TILE_MIXED && G != 0)) {
             return E.fail("chunk mix prefix", ch, G);
+        }
         if (t.kind == TILE_MIXED) {
             // from slot G on the kernel reads shared memory only: every
             // stored element there (padding included) must be a staged index
@@ -215,7 +258,7 @@ bool run_tile(Emu &E, const Tile &t)
             const int32_t dst = P.slot_dst[(size_t)ch * 32 + i];
             if (len < 0 || len > longest) return E.fail("chunk rows not sorted by length", ch, i);
             if (dst == -1 && len != 0) return E.fail("empty slot with elements", ch, i);
-            if (!E.row_sum(t.kind, [off, i](int32_t k) { return off + 32 * (int64_t)k + i; },
+            if (!E.row_sum(kind32, [off, i](int32_t k) { return off + 32 * (int64_t)k + i; },
                            len, s.data()))
                 return false;
             if (!E.store(dst, s.data())) return false;
@@ -295,7 +338,8 @@ extern "C" spmv_status spmv_plan_emulate(const spmv_csr *A, const spmv_perm *per
             const int64_t v[SPMV_EMULATE_STATS] = {
                 (int64_t)P.tiles.size(), P.n_chunk_tiles, P.n_staged_tiles, P.partial_slots,
                 (int64_t)P.fixups.size(), nvr, P.padded_elems, P.use_k1 ? 1 : 0,
-                P.direct_nnz, P.fma_slots, P.mixed_slots, P.staged_entries, two_runs};
+                P.direct_nnz, P.fma_slots, P.mixed_slots, P.staged_entries, two_runs,
+                P.delta_nnz};
             for (int k = 0; k < SPMV_EMULATE_STATS; ++k) stats[k] = v[k];
         }
         return SPMV_OK;

@@ -32,8 +32,24 @@ enum TileKind : int32_t {
     TILE_NARROW = 0,   // every nonzero reads staged x: 16-bit local indices (col16)
     TILE_MIXED = 1,    // col32 >= 0: staged index; col32 < 0: ~global x index
     TILE_GLOBAL = 2,   // col32 = global x index, nothing staged
-    TILE_CHUNK = 3     // elements [e0, e1) of one long row -> partial slot
+    TILE_CHUNK = 3,    // elements [e0, e1) of one long row -> partial slot
+    TILE_DELTA = 4     // nothing staged; chunks whose chunk_mix (the base
+                       // column) is >= 0 store 16-bit column increments in
+                       // col16, the others col32 as in GLOBAL tiles
 };
+
+// Column increments (the colDiff of ICSR, Sec. 2.1, kept per lane): in a
+// chunk of a DELTA tile with base column B, lane i's running column starts at
+// B and element k adds col16 at delta_pos(off, L, k, i); padding elements add
+// 0.  Slots come in pairs, so that a lane reads the increments of two slots
+// with one 32-bit load: slots 2p and 2p+1 of lane i sit at off + 64 p + 2 i
+// and the next entry; when L is odd the last slot keeps the plain layout
+// (off + 32 (L - 1) + i).  off is even.
+inline int64_t delta_pos(int64_t off, int32_t L, int32_t k, int32_t i)
+{
+    if (k < L - (L & 1)) return off + 64 * (int64_t)(k >> 1) + 2 * i + (k & 1);
+    return off + 32 * (int64_t)k + i;
+}
 
 // The staged window of a tile is up to two contiguous runs of x_hat and a
 // gathered list, back to back in shared memory:
@@ -85,7 +101,8 @@ struct HostPlan {
     // K1: CSR.  Tiled forms: elements in chunk order, then the long rows.
     std::vector<int32_t> rowptr;   // K1 only
     std::vector<int32_t> col32;    // K1 / GLOBAL / CHUNK: x index; MIXED: signed
-    std::vector<uint16_t> col16;   // NARROW tiles: shared-memory index
+    std::vector<uint16_t> col16;   // NARROW tiles: shared-memory index; DELTA
+                                   // tiles: column increments
     std::vector<double> val;       // FP64 master values in element order
     std::vector<int32_t> long_rows;  // K1: rows reduced by a whole CTA
 
@@ -93,8 +110,9 @@ struct HostPlan {
     std::vector<int32_t> chunk_off;  // element offset of each chunk
     // MIXED tiles: per chunk, the number of leading element slots that may
     // read x from global memory; every lane's elements from that slot on
-    // are staged (each row stores its gathered elements first).  Other
-    // tiles: 0.
+    // are staged (each row stores its gathered elements first).  DELTA
+    // tiles: the chunk's base column, or -1 for a chunk stored in col32.
+    // Other tiles: 0.
     std::vector<int32_t> chunk_mix;
     std::vector<int32_t> slot_dst;   // 32 per chunk
     std::vector<int32_t> slot_len;   // 32 per chunk (row length, 0 if empty)
@@ -104,6 +122,7 @@ struct HostPlan {
     int64_t partial_slots = 0;
     int32_t n_chunk_tiles = 0, n_staged_tiles = 0, n_global_tiles = 0;
     int64_t staged_entries = 0, list_entries = 0, direct_nnz = 0, narrow_nnz = 0;
+    int64_t delta_nnz = 0;         // nonzeros stored as column increments
     int32_t max_staged = 0;        // most x entries one tile stages
     int64_t padded_elems = 0;      // stored elements (with padding) in chunks
     int64_t fma_slots = 0;         // FMA lanes issued: 32 * (longest row) per chunk,

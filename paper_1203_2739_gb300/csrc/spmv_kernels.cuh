@@ -115,6 +115,18 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t *p)
     return __ldcs(p);
 #endif
 }
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p)
+{
+#if SPMV_STREAM_HINT == 1
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#elif SPMV_STREAM_HINT == 2
+    return __ldg(p);
+#else
+    return __ldcs(p);
+#endif
+}
 __device__ __forceinline__ uint16_t ld_stream(const uint16_t *p)
 {
 #if SPMV_STREAM_HINT == 1
@@ -332,7 +344,9 @@ enum : int {
                      // loads are issued (the unused one reads entry 0) and one
                      // is selected, so a batch has no branch
     FX_SMEM32 = 2,   // col32 is a staged entry
-    FX_SMEM16 = 3    // col16 is a staged entry (narrow tiles)
+    FX_SMEM16 = 3,   // col16 is a staged entry (narrow tiles)
+    FX_DELTA = 4     // col16 holds column increments along the lane's row
+                     // (DELTA tiles): the running column is the x_hat index
 };
 
 template <int FX, int R, typename XT>
@@ -341,7 +355,7 @@ __device__ __forceinline__ void fetch_x(int32_t ci, const XT *seg, const XT *__r
 {
     if constexpr (FX == FX_SMEM16 || FX == FX_SMEM32) {
         load_xrow<R, XT, false>(seg + ci * R, o);
-    } else if constexpr (FX == FX_GLOBAL) {
+    } else if constexpr (FX == FX_GLOBAL || FX == FX_DELTA) {
         load_xrow<R, XT, true>(x + (int64_t)ci * R, o);
     } else {
         const bool g = ci < 0;
@@ -369,12 +383,19 @@ __device__ __forceinline__ int32_t load_col(const int32_t *__restrict__ c32,
 // gathers, and all gathers before the FMAs, so UB gathers per lane are in
 // flight together.  Lanes whose row ended keep their sum (a select, no
 // branch); padding slots hold index 0, a valid entry.
+//
+// FX_DELTA: cc is the lane's running column.  The increments of slots 2p
+// and 2p + 1 sit side by side (chunk start + 64 p + 2 lane), one 32-bit load
+// for both; UB >= 2 batches start on an even slot (the batches of a chunk
+// are U, ..., 4, 2, 1 slots long, U even), and a batch of 1 is the odd last
+// slot, stored plainly.  Padding increments are 0, so a finished lane's
+// column stays on its last entry.
 template <int FX, int UB, int R, typename VT, typename XT>
 __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len,
                                             const VT *__restrict__ val,
                                             const int32_t *__restrict__ c32,
                                             const uint16_t *__restrict__ c16, const XT *seg,
-                                            const XT *__restrict__ x, XT (&s)[R])
+                                            const XT *__restrict__ x, XT (&s)[R], int32_t &cc)
 {
     XT v[UB];
     int32_t ci[UB];
@@ -382,7 +403,29 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
     for (int u = 0; u < UB; ++u) {
         const int64_t e = off + (int64_t)(k0 + u) * 32;
         v[u] = (XT)load_val(val + e);
-        ci[u] = load_col<FX>(c32, c16, e);
+        if constexpr (FX != FX_DELTA) ci[u] = load_col<FX>(c32, c16, e);
+    }
+    if constexpr (FX == FX_DELTA) {
+        if constexpr (UB == 1) {
+            ci[0] = (int32_t)ld_stream(c16 + off + (int64_t)k0 * 32);
+        } else {
+            static_assert(UB % 2 == 0, "increment pairs");
+            // off = chunk start + lane; the pair word of lane i is at
+            // chunk start + 32 k + 2 i
+            const uint32_t *pw = reinterpret_cast<const uint32_t *>(
+                c16 + off + (threadIdx.x & 31) + (int64_t)k0 * 32);
+#pragma unroll
+            for (int j = 0; j < UB / 2; ++j) {
+                const uint32_t w = ld_stream(pw + 32 * j);
+                ci[2 * j] = (int32_t)(w & 0xffffu);
+                ci[2 * j + 1] = (int32_t)(w >> 16);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            cc += ci[u];
+            ci[u] = cc;
+        }
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
@@ -407,30 +450,35 @@ __device__ __forceinline__ void chunk_span(int32_t kb, int32_t ke, int64_t off, 
                                            const VT *__restrict__ val,
                                            const int32_t *__restrict__ c32,
                                            const uint16_t *__restrict__ c16, const XT *seg,
-                                           const XT *__restrict__ x, XT (&s)[R])
+                                           const XT *__restrict__ x, XT (&s)[R], int32_t &cc)
 {
+    static_assert(FX != FX_DELTA || U % 2 == 0, "increment pairs need even batches");
     int32_t k0 = kb;
-    for (; k0 + U <= ke; k0 += U) chunk_batch<FX, U, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+    for (; k0 + U <= ke; k0 += U)
+        chunk_batch<FX, U, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s, cc);
     if constexpr (U > 8) {
         if ((ke - k0) & 8) {
-            chunk_batch<FX, 8, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+            chunk_batch<FX, 8, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s, cc);
             k0 += 8;
         }
     }
     if constexpr (U > 4) {
         if ((ke - k0) & 4) {
-            chunk_batch<FX, 4, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+            chunk_batch<FX, 4, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s, cc);
             k0 += 4;
         }
     }
     if constexpr (U > 2) {
         if ((ke - k0) & 2) {
-            chunk_batch<FX, 2, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+            chunk_batch<FX, 2, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s, cc);
             k0 += 2;
         }
     }
     if constexpr (U > 1) {
-        if ((ke - k0) & 1) chunk_batch<FX, 1, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s);
+        if ((ke - k0) & 1)
+            chunk_batch<FX, 1, R, VT, XT>(k0, off, len, val, c32, c16, seg, x, s, cc);
+    } else {
+        static_assert(FX != FX_DELTA, "increment pairs need even batches");
     }
 }
 
@@ -516,6 +564,7 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
     // register budget)
     constexpr int U = (R == 1 ? (NT == kThreads ? SPMV_U256 : SPMV_WIDE_U) : (R == 2 ? 4 : 2));
     constexpr int FXW = KIND == TILE_NARROW ? FX_SMEM16 : (KIND == TILE_MIXED ? FX_MIXED : FX_GLOBAL);
+    int32_t cc = 0;
 
     const int32_t nv = t.nvrows, nitems = t.nvrows + t.nchunks;
     auto meta = [&](int32_t item) {
@@ -525,7 +574,7 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
             mt.len = __ldg(slot_len + ch * 32 + lane);
             mt.dst = __ldg(slot_dst + ch * 32 + lane);
             mt.off = __ldg(chunk_off + ch);
-            if (KIND == TILE_MIXED) mt.mix = __ldg(chunk_mix + ch);
+            if (KIND == TILE_MIXED || KIND == TILE_DELTA) mt.mix = __ldg(chunk_mix + ch);
         }
         return mt;
     };
@@ -556,12 +605,27 @@ __device__ __forceinline__ void rows_work(const Tile &t, const TileArgs<VT, XT> 
             if constexpr (KIND == TILE_MIXED) {
                 // rows store their gathered elements first: slots [0, G) may
                 // gather, slots [G, L) read shared memory only
-                chunk_span<FX_MIXED, U, R, VT, XT>(0, mc.mix, off, mc.len, val, c32, c16, seg, x, s);
-                chunk_span<FX_SMEM32, U, R, VT, XT>(mc.mix, L, off, mc.len, val, c32, c16, seg, x, s);
+                chunk_span<FX_MIXED, U, R, VT, XT>(0, mc.mix, off, mc.len, val, c32, c16, seg, x, s,
+                                                   cc);
+                chunk_span<FX_SMEM32, U, R, VT, XT>(mc.mix, L, off, mc.len, val, c32, c16, seg, x,
+                                                    s, cc);
             } else if constexpr (KIND == TILE_NARROW) {
-                chunk_span<FX_SMEM16, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x, s);
+                chunk_span<FX_SMEM16, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x, s,
+                                                    cc);
+            } else if constexpr (KIND == TILE_DELTA) {
+                // chunk_mix: the base column (same for the whole warp), or
+                // -1 for a chunk of 32-bit indices
+                if (mc.mix >= 0) {
+                    cc = mc.mix;
+                    chunk_span<FX_DELTA, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x,
+                                                       s, cc);
+                } else {
+                    chunk_span<FX_GLOBAL, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x,
+                                                        s, cc);
+                }
             } else {
-                chunk_span<FX_GLOBAL, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x, s);
+                chunk_span<FX_GLOBAL, U, R, VT, XT>(0, L, off, mc.len, val, c32, c16, seg, x, s,
+                                                    cc);
             }
             store(mc.dst, s);
         }
@@ -607,7 +671,7 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
     }
 
     const int kind = t.kind;
-    if (kind != TILE_GLOBAL) {
+    if (kind == TILE_NARROW || kind == TILE_MIXED) {
         // stage the window: the 16-byte bodies of the two runs by bulk copy
         // (one elected thread, one mbarrier for both), their tails and the
         // gathered list by the CTA's threads
@@ -668,6 +732,7 @@ __device__ __forceinline__ bool tile_work(const Tile &t, const TileArgs<VT, XT> 
     switch (kind) {
     case TILE_NARROW: rows_work<TILE_NARROW, R, VT, XT, NT>(t, A, seg, claim); break;
     case TILE_MIXED: rows_work<TILE_MIXED, R, VT, XT, NT>(t, A, seg, claim); break;
+    case TILE_DELTA: rows_work<TILE_DELTA, R, VT, XT, NT>(t, A, seg, claim); break;
     default: rows_work<TILE_GLOBAL, R, VT, XT, NT>(t, A, seg, claim); break;
     }
     return true;

@@ -5,7 +5,9 @@
 // nonzeros; sHP_RN orders the columns by the parts of a row-net hypergraph
 // partition and the rows into the nested separated block-diagonal form
 // (rows inside one part with it, rows cut at a bisection between its two
-// halves).
+// halves).  The same nesting, applied to the column border of the SB / DB
+// forms a row-side bisection gives, is the nested border order: each
+// bisection's cut columns between its two halves.
 //
 // Vertex ids: rows 0 .. m-1, columns m .. m+n-1.  Ties are broken by the
 // lower id throughout, so every order is deterministic.
@@ -217,16 +219,70 @@ spmv_status order_sbd(const spmv_csr *A, int32_t K, const int32_t *labels, int32
     return SPMV_OK;
 }
 
+// Nested bisection order of the SB / DB forms: labels[m] are row parts in
+// [0, K] (K = the DB row border), the leaves of a bisection tree.  Rows by
+// (part, index), border last.  A column's key comes from the parts of its
+// rows outside the row border: one part k -> 2k; parts a < b -> 2s - 1, s the
+// first leaf of the right half of the bisection that parted a from b (the
+// bits of a and b above their highest differing bit, that bit set); no part
+// -> 2K.
+spmv_status order_nested(const spmv_csr *A, int32_t K, const int32_t *labels, int32_t *row_perm,
+                         int32_t *col_perm)
+{
+    const int32_t m = A->m, n = A->n;
+    if (K < 1 || (K & (K - 1))) {
+        set_error("K=%d must be a power of two", K);
+        return SPMV_E_INVALID;
+    }
+    for (int32_t i = 0; i < m; ++i)
+        if (labels[i] < 0 || labels[i] > K) {
+            set_error("row label %d of row %d outside [0, %d]", labels[i], i, K);
+            return SPMV_E_INVALID;
+        }
+    std::iota(row_perm, row_perm + m, 0);
+    std::stable_sort(row_perm, row_perm + m,
+                     [&](int32_t a, int32_t b) { return labels[a] < labels[b]; });
+    std::vector<int32_t> lo((size_t)n, K), hi((size_t)n, -1);
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t l = labels[i];
+        if (l == K) continue;
+        for (int32_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
+            const int32_t c = A->colidx[p];
+            lo[(size_t)c] = std::min(lo[(size_t)c], l);
+            hi[(size_t)c] = std::max(hi[(size_t)c], l);
+        }
+    }
+    std::vector<int64_t> key((size_t)n);
+    for (int32_t j = 0; j < n; ++j) {
+        const int32_t a = lo[(size_t)j], b = hi[(size_t)j];
+        if (b < 0) {
+            key[(size_t)j] = 2 * (int64_t)K;
+        } else if (a == b) {
+            key[(size_t)j] = 2 * (int64_t)a;
+        } else {
+            const int32_t hb = 31 - __builtin_clz((unsigned)(a ^ b));
+            const int64_t s = ((int64_t)b >> hb) << hb;
+            key[(size_t)j] = 2 * s - 1;
+        }
+    }
+    std::iota(col_perm, col_perm + n, 0);
+    std::stable_sort(col_perm, col_perm + n,
+                     [&](int32_t a, int32_t b) { return key[(size_t)a] < key[(size_t)b]; });
+    return SPMV_OK;
+}
+
 spmv_status reorder(const spmv_csr *A, int32_t method, int32_t K, const int32_t *labels,
                     int32_t *row_perm, int32_t *col_perm)
 {
     spmv_status st = validate_csr(A);
     if (st != SPMV_OK) return st;
-    if (!row_perm || !col_perm || (method == SPMV_ORDER_SBD && !labels && A->n > 0)) {
+    if (!row_perm || !col_perm || (method == SPMV_ORDER_SBD && !labels && A->n > 0) ||
+        (method == SPMV_ORDER_NESTED && !labels && A->m > 0)) {
         set_error("NULL argument");
         return SPMV_E_INVALID;
     }
     if (method == SPMV_ORDER_SBD) return order_sbd(A, K, labels, row_perm, col_perm);
+    if (method == SPMV_ORDER_NESTED) return order_nested(A, K, labels, row_perm, col_perm);
     if (method != SPMV_ORDER_BFS && method != SPMV_ORDER_RCM) {
         set_error("unknown ordering %d", method);
         return SPMV_E_INVALID;
@@ -242,12 +298,11 @@ spmv_status reorder(const spmv_csr *A, int32_t method, int32_t K, const int32_t 
 }  // namespace spmv
 
 extern "C" spmv_status spmv_reorder(const spmv_csr *A, int32_t method, int32_t K,
-                                    const int32_t *col_labels, int32_t *row_perm,
-                                    int32_t *col_perm)
+                                    const int32_t *labels, int32_t *row_perm, int32_t *col_perm)
 {
     spmv::clear_error();
     try {
-        return spmv::reorder(A, method, K, col_labels, row_perm, col_perm);
+        return spmv::reorder(A, method, K, labels, row_perm, col_perm);
     } catch (const std::bad_alloc &) {
         spmv::set_error("out of host memory");
         return SPMV_E_NOMEM;

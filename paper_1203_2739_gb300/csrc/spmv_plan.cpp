@@ -215,6 +215,7 @@ struct TileCfg {
     int32_t entry_bytes;  // bytes of one x entry (r values)
     int32_t list_min;   // uses in the tile that put a column outside the run on the list
     bool stage;         // staging allowed
+    bool delta;         // chunks of unstaged tiles store column increments
 };
 
 // Cuts the plan rows of the parts into tiles of consecutive rows with a
@@ -514,9 +515,18 @@ struct Tiler {
         const int32_t nrows = (int32_t)order.size();
         t.nchunks = (nrows + 31) / 32;
         std::vector<int32_t> seq;
+        const bool delta = cfg.delta && t.kind == TILE_GLOBAL;
+        int32_t n_delta = 0;
         for (int32_t c = 0; c < t.nchunks; ++c) {
             const int32_t first = c * 32;
             const int32_t L = prp[order[first] + 1] - prp[order[first]];
+            if (delta && (P.val.size() & 1)) {
+                // increments are read in 32-bit pairs: the chunk starts on
+                // an even element
+                P.val.push_back(0.0);
+                P.col32.push_back(0);
+                P.col16.push_back(0);
+            }
             const size_t off = P.val.size();
             P.chunk_off.push_back((int32_t)off);
             P.val.resize(off + (size_t)L * 32, 0.0);
@@ -551,8 +561,54 @@ struct Tiler {
                 }
                 for (int32_t k = 0; k < len; ++k) put(off + (size_t)k * 32 + i, seq[k]);
             }
+            if (delta) {
+                // base column: the smallest first column of the chunk's
+                // rows; every increment (from the base to a row's first
+                // column, then between successive columns of the row) must
+                // fit 16 bits
+                int32_t B = INT32_MAX;
+                bool fits = true;
+                for (int32_t i = 0; i < 32 && first + i < nrows; ++i) {
+                    const int32_t r = order[first + i];
+                    if (prp[r + 1] > prp[r]) B = std::min(B, col[prp[r]]);
+                }
+                if (B == INT32_MAX) B = 0;
+                for (int32_t i = 0; i < 32 && first + i < nrows && fits; ++i) {
+                    const int32_t r = order[first + i];
+                    int32_t prev = B;
+                    for (int32_t q = prp[r]; q < prp[r + 1]; ++q) {
+                        const int64_t d = (int64_t)col[q] - prev;
+                        if (d < 0 || d > 65535) {
+                            fits = false;
+                            break;
+                        }
+                        prev = col[q];
+                    }
+                }
+                if (fits) {
+                    for (int32_t i = 0; i < 32 && first + i < nrows; ++i) {
+                        const int32_t r = order[first + i];
+                        int32_t prev = B;
+                        for (int32_t k = 0; k < prp[r + 1] - prp[r]; ++k) {
+                            const int32_t cg = col[prp[r] + k];
+                            P.col16[(size_t)delta_pos((int64_t)off, L, k, i)] =
+                                (uint16_t)(cg - prev);
+                            prev = cg;
+                        }
+                        P.delta_nnz += prp[r + 1] - prp[r];
+                    }
+                    ++n_delta;
+                }
+                G = fits ? B : -1;
+            }
             P.chunk_mix.push_back(G);
-            P.mixed_slots += (int64_t)G * 32;
+            if (!delta) P.mixed_slots += (int64_t)G * 32;
+        }
+        if (delta && n_delta > 0) {
+            t.kind = TILE_DELTA;
+        } else if (delta) {
+            // no chunk fits: a plain GLOBAL tile
+            std::fill(P.chunk_mix.begin() + t.chunk0, P.chunk_mix.end(), 0);
         }
         P.tiles.push_back(t);
     }
@@ -681,7 +737,8 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
     P->dtype = o.dtype;
     P->nrhs = r;
     if (o.flags & ~(SPMV_FLAG_NO_STAGING | SPMV_FLAG_TILED_NATURAL | SPMV_FLAG_SM_AFFINE |
-                    SPMV_FLAG_PERSISTENT | SPMV_FLAG_STAGE | SPMV_FLAG_TEST_WAIT_EXPIRES)) {
+                    SPMV_FLAG_PERSISTENT | SPMV_FLAG_STAGE | SPMV_FLAG_TEST_WAIT_EXPIRES |
+                    SPMV_FLAG_COL_DELTA)) {
         set_error("unknown flag bits 0x%x", o.flags);
         return SPMV_E_INVALID;
     }
@@ -864,6 +921,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         cfg.long_t = o.long_row > 0 ? o.long_row : std::max<int32_t>(1024, cfg.tnnz / 16);
     }
     cfg.stage = !(o.flags & SPMV_FLAG_NO_STAGING) && (wide || mid || (o.flags & SPMV_FLAG_STAGE));
+    cfg.delta = (o.flags & SPMV_FLAG_COL_DELTA) != 0;
     P->lanes = 32;                 // one lane per row, 32 rows per chunk
     P->long_thresh = cfg.long_t;
 
@@ -960,7 +1018,7 @@ spmv_status build_host_plan(const spmv_csr *A, const spmv_perm *perm,
         set_error("too many stored elements");
         return SPMV_E_UNSUPPORTED;
     }
-    if (P->narrow_nnz == 0) {
+    if (P->narrow_nnz == 0 && P->delta_nnz == 0) {
         P->col16.clear();
         P->col16.shrink_to_fit();
     }

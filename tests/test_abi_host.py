@@ -89,7 +89,7 @@ def test_plan_create_validation_before_any_device_call():
     assert st == S.SPMV_E_INVALID and "cta_threads" in msg
     st, msg = _plan_status(cta_threads=1024, flags=S.SPMV_FLAG_PERSISTENT | 2)
     assert st == S.SPMV_E_INVALID
-    st, msg = _plan_status(flags=64)
+    st, msg = _plan_status(flags=128)
     assert st == S.SPMV_E_INVALID and "flag" in msg
     st, msg = _plan_status(flags=S.SPMV_FLAG_SM_AFFINE | S.SPMV_FLAG_PERSISTENT)
     assert st == S.SPMV_E_INVALID and "flag" in msg.lower()

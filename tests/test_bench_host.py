@@ -290,3 +290,32 @@ def test_shape_map_from_object_or_bench_line(tmp_path):
     line.write_text("log line\n" + json.dumps({"detail": {
         "a/sb1024": {"tile_shape": "cta1024"}, "a/natural": {"tile_shape": None}}}) + "\n")
     assert bench.load_shape_map(str(line)) == {"a/sb1024": "cta1024"}
+
+
+def test_increment_and_nested_forms():
+    """"<form>_icsr" is <form> with SPMV_FLAG_COL_DELTA; "sbnest<K>" and
+    "dbnest<K>" reuse the CN / eRCN partition of "sb<K>" / "db<K>" with the
+    nested border order through the tiled kernel."""
+    m = n = 2500
+    rp, ci, _ = synth.mesh5(50, seed=2)
+    parts = bench.partition_jobs(S, rp, ci, ["sb8_icsr", "dbnest8", "split4_icsr"], 0, 2)
+    assert set(parts) == {("cn", 8), ("ercn", 8), ("rcn", 256)}
+    kw, _ = bench.form_kwargs(S, "sb8_icsr", rp, ci, parts)
+    kw0, _ = bench.form_kwargs(S, "sb8", rp, ci, parts)
+    assert kw["flags"] == S.SPMV_FLAG_COL_DELTA and kw0.get("flags", 0) == 0
+    assert np.array_equal(kw["col_perm"], kw0["col_perm"])
+    kw, _ = bench.form_kwargs(S, "split16_icsr", rp, ci, parts)
+    assert kw["flags"] == S.SPMV_FLAG_COL_DELTA and kw["K"] == 16
+    for f, key in (("sbnest8", ("cn", 8)), ("dbnest8_icsr", ("ercn", 8))):
+        if key not in parts:
+            parts.update(bench.partition_jobs(S, rp, ci, [f], 0, 2))
+        kw, r = bench.form_kwargs(S, f, rp, ci, parts)
+        want = S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, 8, r["labels"])
+        assert np.array_equal(kw["row_perm"], want[0]) and np.array_equal(kw["col_perm"], want[1])
+        assert kw["flags"] & S.SPMV_FLAG_TILED_NATURAL
+        assert bool(kw["flags"] & S.SPMV_FLAG_COL_DELTA) == f.endswith("_icsr")
+    with pytest.raises(ValueError):
+        bench.form_kwargs(S, "natural_icsr", rp, ci, parts)
+    g = bench.reorder_gains({"a/tiled": {"us": 8.0}, "a/sb8": {"us": 4.0},
+                             "a/sb8_icsr": {"us": 3.2}})["a"]
+    assert g["icsr_gain"] == {"sb8": 1.25}

@@ -158,3 +158,89 @@ def test_row_net_partition_gives_the_sbd_order():
     assert out["cost"] == lam
     with pytest.raises(S.SpmvError):
         S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_SBD, 12, out["labels"])
+
+
+# ------------------------------------------------ nested border order ---
+def test_golden_nested_border_order():
+    s = json.load(open(GOLDEN))["nested"]
+    rp, ci, _ = _from_rows(s["m"], s["n"], s["rows"])
+    r, c = OO.nested_order(s["m"], s["n"], rp, ci, s["K"], s["row_labels"])
+    assert r.tolist() == s["row_perm"] and c.tolist() == s["col_perm"]
+    got = S.spmv_reorder(s["m"], s["n"], rp, ci, S.SPMV_ORDER_NESTED, s["K"], s["row_labels"])
+    assert got[0].tolist() == s["row_perm"] and got[1].tolist() == s["col_perm"]
+
+
+def _transpose(m, n, rp, ci):
+    r = np.repeat(np.arange(m), np.diff(rp))
+    return synth.coo_to_csr(n, m, ci.astype(np.int64), r.astype(np.int64), np.ones(r.size))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nested_order_is_the_sbd_order_of_the_transpose(seed):
+    """Without a row border the nested order of A from row parts is the
+    separated block-diagonal order of A^T from the same labels on its
+    columns, rows and columns exchanged (the pinned sbd_order)."""
+    m, n, K = 45, 38, 8
+    rp, ci, _ = synth.random_sparse(m, n, 0.06, seed, empty_rows=0.1)
+    lab = synth.random_labels(m, K, seed + 7)
+    tp, tc, _ = _transpose(m, n, rp, ci)
+    r, c = OO.nested_order(m, n, rp, ci, K, lab)
+    tr, tcol = OO.sbd_order(n, m, tp, tc, K, lab)
+    assert np.array_equal(r, tcol) and np.array_equal(c, tr)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nested_border_sits_between_the_halves(seed):
+    """Brute force on the permuted matrix: every column whose rows span parts
+    a < b comes after every column of the parts left of the bisection that
+    split them and before every column of the parts right of it; R_B rows
+    and the columns only R_B touches come last."""
+    m, n, K = 60, 50, 8
+    rp, ci, _ = synth.random_sparse(m, n, 0.05, seed, empty_rows=0.1)
+    lab = synth.random_labels(m, K, seed + 9, border_frac=0.1)
+    r, c = OO.nested_order(m, n, rp, ci, K, lab)
+    assert [lab[i] for i in r] == sorted(lab)
+    pos = np.empty(n, dtype=np.int64)
+    pos[c] = np.arange(n)
+    spans = {}
+    for i in range(m):
+        if lab[i] == K:
+            continue
+        for p in range(rp[i], rp[i + 1]):
+            spans.setdefault(int(ci[p]), set()).add(int(lab[i]))
+    untouched = [j for j in range(n) if j not in spans]
+    assert sorted(pos[untouched].tolist()) == list(range(n - len(untouched), n))
+    for j, parts in spans.items():
+        a, b = min(parts), max(parts)
+        if a == b:
+            continue
+        size = 2
+        while a // size != b // size:
+            size *= 2
+        lo = a // size * size
+        mid = lo + size // 2
+        for k, ps in spans.items():
+            if len(ps) == 1:
+                (q,) = ps
+                if lo <= q < mid:
+                    assert pos[k] < pos[j]
+                elif mid <= q < lo + size:
+                    assert pos[k] > pos[j]
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("shape", [(40, 40), (37, 51), (60, 23)])
+def test_library_nested_order_equals_the_oracle(seed, shape):
+    m, n = shape
+    rp, ci, _ = synth.random_sparse(m, n, 0.05, seed, empty_rows=0.15)
+    for K, frac in ((8, 0.0), (16, 0.15), (1, 0.2)):
+        lab = synth.random_labels(m, K, seed + 5, border_frac=frac)
+        got = S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, K, lab)
+        want = OO.nested_order(m, n, rp, ci, K, lab)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    with pytest.raises(S.SpmvError):
+        S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, 12, synth.random_labels(m, 12, 1))
+    with pytest.raises(S.SpmvError):
+        bad = synth.random_labels(m, 8, 2)
+        bad[0] = 9
+        S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, 8, bad)

@@ -201,3 +201,99 @@ def test_emulation_reports_validation_errors_like_plan_creation():
     with pytest.raises(S.SpmvError) as e:
         S.spmv_plan_emulate(20, 20, rp, ci, v, np.zeros(20), row_perm=bad, col_perm=None)
     assert e.value.status == S.SPMV_E_STRUCTURE
+
+
+def _with_flags(kw, flags):
+    out = dict(kw)
+    out["flags"] = out.get("flags", 0) | flags
+    return out
+
+
+@pytest.mark.parametrize("name", list(MATRICES))
+def test_column_increments_every_form_and_shape(name):
+    """SPMV_FLAG_COL_DELTA: the chunks of tiles that stage nothing hold 16-bit
+    column increments along each row (ICSR's colDiff, Sec. 2.1, per lane,
+    slots in pairs).  The emulator decodes them as the kernel does, checks
+    every running column (padding included) against n and every padding
+    increment for 0, and the product must stay exact."""
+    rp, ci, _ = MATRICES[name]()
+    m = n = len(rp) - 1
+    v = _integer(rp, ci, 21)
+    x = synth.integer_x(n, 22)
+    y_ref = _reference(m, n, rp, ci, v, x)
+    nnz = int(rp[-1])
+    shapes = _shapes(S.SPMV_F64, 1, nnz)
+    total = 0
+    for shape in SHAPE_NAMES:
+        st = _check(m, n, rp, ci, v, x, y_ref,
+                    **_with_flags(shapes[shape], S.SPMV_FLAG_TILED_NATURAL |
+                                  S.SPMV_FLAG_COL_DELTA))
+        total += st["delta_nnz"]
+        for form, kw in _forms(m, n, rp, ci, 64, 16, 23):
+            st = _check(m, n, rp, ci, v, x, y_ref,
+                        **_with_flags(shapes[shape], S.SPMV_FLAG_COL_DELTA), **kw)
+            assert 0 <= st["delta_nnz"] <= st["gathered_nnz"]
+            total += st["delta_nnz"]
+            # without the flag nothing is increment-coded
+            st0 = _check(m, n, rp, ci, v, x, y_ref, **shapes[shape], **kw)
+            assert st0["delta_nnz"] == 0
+    assert total > 0
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 4, 8])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_column_increments_layouts(dtype, nrhs):
+    """Batches of 8, 4 and 2 slots (one per r) read the increments in pairs;
+    rows of every length up to 40 give chunks of odd and even length."""
+    rng = np.random.default_rng(24 + nrhs)
+    m, n = 3000, 5000
+    lens = rng.integers(0, 41, size=m)
+    rp = np.zeros(m + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(lens)
+    ci = np.concatenate([np.sort(rng.choice(n, size=k, replace=False)) for k in lens]
+                        ).astype(np.int32)
+    v = _integer(rp, ci, 25)
+    x = synth.integer_x(n, 26, nrhs=nrhs) if nrhs > 1 else synth.integer_x(n, 26)
+    y_ref = _reference(m, n, rp, ci, v, x)
+    shapes = _shapes(dtype, nrhs, int(rp[-1]))
+    for shape in ("cta256", "cta256w", "cta512", "cta1024"):
+        st = _check(m, n, rp, ci, v, x, y_ref,
+                    **_with_flags(shapes[shape], S.SPMV_FLAG_TILED_NATURAL |
+                                  S.SPMV_FLAG_COL_DELTA))
+        # n < 65536: every chunk of an unstaged tile fits 16 bits
+        assert st["delta_nnz"] == st["gathered_nnz"] - _warp_row_nnz(rp, shapes[shape]), shape
+
+
+def _warp_row_nnz(rp, shape):
+    """Nonzeros of rows reduced by a whole warp (never increment-coded)."""
+    lens = np.diff(rp)
+    return int(lens[lens > shape.get("warp_rows", 64)].sum())
+
+
+def test_column_increments_fall_back_on_wide_rows():
+    """Rows whose successive columns lie more than 65535 apart keep 32-bit
+    indices (their chunk's base is -1); the rest of the tile is still
+    increment-coded, and the product is unchanged."""
+    rng = np.random.default_rng(27)
+    m, n = 4096, 400000
+    lens = rng.integers(2, 9, size=m)
+    rows = []
+    for i, k in enumerate(lens):
+        if i % 3 == 0:
+            rows.append(np.sort(rng.choice(n, size=k, replace=False)))        # wide
+        else:
+            c0 = rng.integers(0, n - 2000)
+            rows.append(np.sort(c0 + rng.choice(2000, size=k, replace=False)))  # narrow
+    rp = np.zeros(m + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(lens)
+    ci = np.concatenate(rows).astype(np.int32)
+    v = _integer(rp, ci, 28)
+    x = synth.integer_x(n, 29)
+    y_ref = _reference(m, n, rp, ci, v, x)
+    # rows sorted by length share chunks: a chunk mixes wide and narrow rows
+    # and falls back; the base of 32 narrow rows spread over n does not fit
+    # either, so order the rows by their first column first
+    order = np.argsort(ci[rp[:-1]], kind="stable").astype(np.int32)
+    st = _check(m, n, rp, ci, v, x, y_ref, row_perm=order,
+                flags=S.SPMV_FLAG_TILED_NATURAL | S.SPMV_FLAG_COL_DELTA)
+    assert 0 <= st["delta_nnz"] < st["gathered_nnz"]
