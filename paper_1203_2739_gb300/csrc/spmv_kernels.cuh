@@ -67,6 +67,13 @@ constexpr int kWideThreads = 1024;
 #ifndef SPMV_U256
 #define SPMV_U256 8
 #endif
+//   SPMV_PRED_PAD     1 = a lane whose row has ended issues no load, gather
+//                     or FMA for the chunk's remaining slots; 0 = every lane
+//                     loads every slot up to the chunk's longest row and
+//                     discards the padding's products
+#ifndef SPMV_PRED_PAD
+#define SPMV_PRED_PAD 1
+#endif
 //   SPMV_L1_PREF      1 = ask for the largest L1 carveout for the tile kernels
 #ifndef SPMV_L1_PREF
 #define SPMV_L1_PREF 0
@@ -381,8 +388,12 @@ __device__ __forceinline__ int32_t load_col(const int32_t *__restrict__ c32,
 // row, so every slot exists for the warp): element k of lane i is at
 // off + 32 k + i.  All UB value / index loads are issued before the UB
 // gathers, and all gathers before the FMAs, so UB gathers per lane are in
-// flight together.  Lanes whose row ended keep their sum (a select, no
-// branch); padding slots hold index 0, a valid entry.
+// flight together.  A lane whose row has ended issues no load and no gather
+// for the slot (per-lane predicates, no branch): rows are sorted longest
+// first, so the padding of a slot is its top lanes and whole sectors of the
+// stream are never requested.  Padding slots hold index 0 all the same: the
+// mixed path (two loads per slot) keeps every lane's loads and selects its
+// sums, which fits the 256-thread register budget.
 //
 // FX_DELTA: cc is the lane's running column.  The increments of slots 2p
 // and 2p + 1 sit side by side (chunk start + 64 p + 2 lane), one 32-bit load
@@ -402,12 +413,17 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
         const int64_t e = off + (int64_t)(k0 + u) * 32;
-        v[u] = (XT)load_val(val + e);
-        if constexpr (FX != FX_DELTA) ci[u] = load_col<FX>(c32, c16, e);
+        v[u] = XT(0);
+        ci[u] = 0;
+        if (FX == FX_MIXED || !SPMV_PRED_PAD || k0 + u < len) {
+            v[u] = (XT)load_val(val + e);
+            if constexpr (FX != FX_DELTA) ci[u] = load_col<FX>(c32, c16, e);
+        }
     }
     if constexpr (FX == FX_DELTA) {
         if constexpr (UB == 1) {
-            ci[0] = (int32_t)ld_stream(c16 + off + (int64_t)k0 * 32);
+            if (!SPMV_PRED_PAD || k0 < len)
+                ci[0] = (int32_t)ld_stream(c16 + off + (int64_t)k0 * 32);
         } else {
             static_assert(UB % 2 == 0, "increment pairs");
             // off = chunk start + lane; the pair word of lane i is at
@@ -416,7 +432,8 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
                 c16 + off + (threadIdx.x & 31) + (int64_t)k0 * 32);
 #pragma unroll
             for (int j = 0; j < UB / 2; ++j) {
-                const uint32_t w = ld_stream(pw + 32 * j);
+                uint32_t w = 0;       // a pair past the row's end adds 0
+                if (!SPMV_PRED_PAD || k0 + 2 * j < len) w = ld_stream(pw + 32 * j);
                 ci[2 * j] = (int32_t)(w & 0xffffu);
                 ci[2 * j + 1] = (int32_t)(w >> 16);
             }
@@ -429,13 +446,20 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
     }
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
-        XT xo[R];
-        fetch_x<FX, R, XT>(ci[u], seg, x, xo);
         const bool on = k0 + u < len;
+        if constexpr (FX == FX_MIXED || !SPMV_PRED_PAD) {
+            XT xo[R];
+            fetch_x<FX, R, XT>(ci[u], seg, x, xo);
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            const XT f = fma(v[u], xo[c], s[c]);
-            s[c] = on ? f : s[c];
+            for (int c = 0; c < R; ++c) {
+                const XT f = fma(v[u], xo[c], s[c]);
+                s[c] = on ? f : s[c];
+            }
+        } else if (on) {
+            XT xo[R];
+            fetch_x<FX, R, XT>(ci[u], seg, x, xo);
+#pragma unroll
+            for (int c = 0; c < R; ++c) s[c] = fma(v[u], xo[c], s[c]);
         }
     }
 }
