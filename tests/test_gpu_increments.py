@@ -158,3 +158,34 @@ def test_same_product_as_32_bit_indices(mesh):
         inc = _plan(m, n, rp, ci, v, kw)
         assert inc.info["n_tiles"] == plain.info["n_tiles"]
         assert np.array_equal(run_plan(S, inc, x), run_plan(S, plain, x))
+
+
+def test_degenerate_matrices():
+    """No nonzeros, one nonzero, and a tall matrix with three columns (every
+    increment 0, 1 or 2) under the increment flag, in the natural and split
+    forms."""
+    m, n = 37, 11
+    rp = np.zeros(m + 1, dtype=np.int32)
+    ci = np.zeros(0, dtype=np.int32)
+    v = np.zeros(0)
+    plan = _plan(m, n, rp, ci, v, dict(flags=S.SPMV_FLAG_TILED_NATURAL))
+    assert np.array_equal(run_plan(S, plan, synth.uniform_x(n, 0)), np.zeros(m))
+    plan = _plan(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]),
+                 dict(flags=S.SPMV_FLAG_TILED_NATURAL))
+    assert run_plan(S, plan, np.array([2.0]))[0] == 6.0
+    m, n = 10000, 3
+    rng = np.random.default_rng(60)
+    rows = [np.sort(rng.choice(n, size=rng.integers(0, 4), replace=False)) for _ in range(m)]
+    rp = np.zeros(m + 1, dtype=np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate(rows).astype(np.int32)
+    vi = synth.integer_values(int(rp[-1]), 61)
+    x = synth.integer_x(n, 62)
+    nzl = synth.random_labels(int(rp[-1]), 4, 63)
+    rperm, cperm, rpp, cpp = S.spmv_form_from_labels(m, n, rp, ci, S.SPMV_SPLIT, 4, nzl)
+    for kw in (dict(flags=S.SPMV_FLAG_TILED_NATURAL),
+               dict(row_perm=rperm, col_perm=cperm, form=S.SPMV_SPLIT, K=4,
+                    row_part_ptr=rpp, col_part_ptr=cpp, nz_part=nzl)):
+        plan = _plan(m, n, rp, ci, vi, kw)
+        assert plan.info["delta_nnz"] == int(rp[-1])
+        _check(plan, m, n, rp, ci, vi, x, exact=True)
