@@ -67,10 +67,11 @@ constexpr int kWideThreads = 1024;
 #ifndef SPMV_U256
 #define SPMV_U256 8
 #endif
-//   SPMV_PRED_PAD     1 = a lane whose row has ended issues no load, gather
-//                     or FMA for the chunk's remaining slots; 0 = every lane
-//                     loads every slot up to the chunk's longest row and
-//                     discards the padding's products
+//   SPMV_PRED_PAD     1 = with FP64 values, a lane whose row has ended issues
+//                     no load, gather or FMA for the chunk's remaining slots;
+//                     0 (and FP32 / BF16 values) = every lane loads every
+//                     slot up to the chunk's longest row and discards the
+//                     padding's products
 #ifndef SPMV_PRED_PAD
 #define SPMV_PRED_PAD 1
 #endif
@@ -393,7 +394,8 @@ __device__ __forceinline__ int32_t load_col(const int32_t *__restrict__ c32,
 // first, so the padding of a slot is its top lanes and whole sectors of the
 // stream are never requested.  Padding slots hold index 0 all the same: the
 // mixed path (two loads per slot) keeps every lane's loads and selects its
-// sums, which fits the 256-thread register budget.
+// sums, which fits the 256-thread register budget, and so do FP32 / BF16
+// values (measured faster that way).
 //
 // FX_DELTA: cc is the lane's running column.  The increments of slots 2p
 // and 2p + 1 sit side by side (chunk start + 64 p + 2 lane), one 32-bit load
@@ -408,6 +410,9 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
                                             const uint16_t *__restrict__ c16, const XT *seg,
                                             const XT *__restrict__ x, XT (&s)[R], int32_t &cc)
 {
+    // padding lanes skip their loads with FP64 values only: with FP32 /
+    // BF16 values the predicated form timed 3-7% slower
+    constexpr bool PRED = SPMV_PRED_PAD && FX != FX_MIXED && std::is_same<VT, double>::value;
     XT v[UB];
     int32_t ci[UB];
 #pragma unroll
@@ -415,15 +420,14 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
         const int64_t e = off + (int64_t)(k0 + u) * 32;
         v[u] = XT(0);
         ci[u] = 0;
-        if (FX == FX_MIXED || !SPMV_PRED_PAD || k0 + u < len) {
+        if (!PRED || k0 + u < len) {
             v[u] = (XT)load_val(val + e);
             if constexpr (FX != FX_DELTA) ci[u] = load_col<FX>(c32, c16, e);
         }
     }
     if constexpr (FX == FX_DELTA) {
         if constexpr (UB == 1) {
-            if (!SPMV_PRED_PAD || k0 < len)
-                ci[0] = (int32_t)ld_stream(c16 + off + (int64_t)k0 * 32);
+            if (!PRED || k0 < len) ci[0] = (int32_t)ld_stream(c16 + off + (int64_t)k0 * 32);
         } else {
             static_assert(UB % 2 == 0, "increment pairs");
             // off = chunk start + lane; the pair word of lane i is at
@@ -433,7 +437,7 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
 #pragma unroll
             for (int j = 0; j < UB / 2; ++j) {
                 uint32_t w = 0;       // a pair past the row's end adds 0
-                if (!SPMV_PRED_PAD || k0 + 2 * j < len) w = ld_stream(pw + 32 * j);
+                if (!PRED || k0 + 2 * j < len) w = ld_stream(pw + 32 * j);
                 ci[2 * j] = (int32_t)(w & 0xffffu);
                 ci[2 * j + 1] = (int32_t)(w >> 16);
             }
@@ -447,7 +451,7 @@ __device__ __forceinline__ void chunk_batch(int32_t k0, int64_t off, int32_t len
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
         const bool on = k0 + u < len;
-        if constexpr (FX == FX_MIXED || !SPMV_PRED_PAD) {
+        if constexpr (!PRED) {
             XT xo[R];
             fetch_x<FX, R, XT>(ci[u], seg, x, xo);
 #pragma unroll
