@@ -169,3 +169,27 @@ def test_scale_mesh_sb():
     shapes = {k: shapes[k] for k in ("cta256", "cta256x8", "cta1024")}
     _check_plans("mesh6144/sb", _build_all(m, n, rp, ci, v, kw, shapes), x, rows, y_ref, absax,
                  TOL[0])
+
+
+NESTED_ICSR_FORMS = ["sbnest1024", "dbnest1024", "bfs_icsr", "sb1024_icsr", "sbnest1024_icsr",
+                     "split16_icsr", "split256_icsr"]
+
+
+@pytest.mark.parametrize("name", SWEEP)
+def test_nested_border_and_increment_forms(sweep, name):
+    """The nested border order (SB and DB partitions of the sweep, each
+    bisection's cut columns between its halves) and the 16-bit column
+    increments of unstaged chunks, on the sweep's full-size plans, in the
+    unstaged shapes and the wide staged one; FP64, and BF16 for two of them."""
+    rp, ci, v, parts = sweep[name]
+    m = n = len(rp) - 1
+    x = synth.uniform_x(n, 5)
+    rows = _sample(m, seed=21)
+    y_ref, absax = oracle.spmv_rows(rp, ci, v, x, rows)
+    for dtype, forms in ((0, NESTED_ICSR_FORMS), (2, ["sbnest1024_icsr", "split16_icsr"])):
+        shapes = bench.tile_shapes(S, dtype, 1, int(rp[-1]))
+        shapes = {k: shapes[k] for k in ("cta256", "cta256w", "cta256x8", "cta1024")}
+        for f in forms:
+            kw, _ = bench.form_kwargs(S, f, rp, ci, parts)
+            _check_plans("%s/%s/%d" % (name, f, dtype), _build_all(m, n, rp, ci, v, kw, shapes),
+                         x, rows, y_ref, absax, TOL[dtype])
