@@ -24,6 +24,12 @@ What each function restates (the C file ``ref.c`` holds the loops):
 * ``cachesim_*``      fully associative LRU cache misses of the CSR access order.
 * ``cg``              FP64 conjugate gradients.
 
+Two plain-Python modules sit beside it: ``order.py`` (the comparison orders
+sBFS, sRCM and sHP_RN of Sec. 5.1, and the nested order of the SB / DB
+border) and ``icsr.py`` (ICSR's colDiff and rowJump, Sec. 2.1, with the
+product loop over them), pinned in ``tests/test_orders.py`` and
+``tests/test_icsr_oracle.py``.
+
 Pins (``tests/test_oracle_pins.py``, run with ``-m "not gpu"``): brute-force
 dense products with exact integer data, the Laplacian's closed-form
 eigenvectors and row sums, exact permutation and split identities,
