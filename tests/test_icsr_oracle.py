@@ -56,3 +56,30 @@ def test_empty_and_single_row():
     assert IC.icsr_spmv(4, 3, [], [], [], [1, 2, 3]).tolist() == [0, 0, 0, 0]
     cd, rj = IC.icsr_encode(3, 5, [0, 0, 0, 3], [0, 2, 4])
     assert cd.tolist() == [0, 2, 2] and rj.tolist() == [2]
+
+
+def test_fixture_catches_planted_mistakes():
+    """The hand-worked fixture separates the oracle from plausible wrong
+    readings: no extra n at a row change (the loop cannot see row ends),
+    absolute row indices in rowJump instead of increments, and a running
+    column that restarts at every row."""
+    g = json.load(open(GOLDEN))
+    rp, ci = _csr(g["m"], g["n"], g["rows"])
+    cd, rj = IC.icsr_encode(g["m"], g["n"], rp, ci)
+
+    def no_signal(m, n, rowptr, colidx):
+        c = np.asarray(colidx, dtype=np.int64)
+        return np.diff(np.r_[0, c]), IC.icsr_encode(m, n, rowptr, colidx)[1]
+
+    def absolute_rows(m, n, rowptr, colidx):
+        d, _ = IC.icsr_encode(m, n, rowptr, colidx)
+        return d, np.flatnonzero(np.diff(np.asarray(rowptr)))
+
+    def restart_per_row(m, n, rowptr, colidx):
+        return np.asarray(colidx, dtype=np.int64), IC.icsr_encode(m, n, rowptr, colidx)[1]
+
+    for wrong in (no_signal, absolute_rows, restart_per_row):
+        wd, wj = wrong(g["m"], g["n"], rp, ci)
+        assert (wd.tolist(), wj.tolist()) != (g["col_diff"], g["row_jump"]), wrong.__name__
+    y = IC.icsr_spmv(g["m"], g["n"], cd, rj, g["vals"], g["x"])
+    assert y.tolist() == g["y"]

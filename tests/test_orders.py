@@ -244,3 +244,46 @@ def test_library_nested_order_equals_the_oracle(seed, shape):
         bad = synth.random_labels(m, 8, 2)
         bad[0] = 9
         S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, 8, bad)
+
+
+def test_nested_fixture_catches_planted_mistakes():
+    """The nested fixture separates the oracle from plausible wrong readings:
+    counting R_B's rows in a column's parts, placing a cut column by its
+    lowest part instead of its bisection, and leaving untouched columns in
+    index order among the others."""
+    s = json.load(open(GOLDEN))["nested"]
+    rp, ci, _ = _from_rows(s["m"], s["n"], s["rows"])
+    m, n, K, lab = s["m"], s["n"], s["K"], s["row_labels"]
+
+    def parts_of(j, with_border):
+        return [lab[i] for i in range(m) for p in range(rp[i], rp[i + 1])
+                if ci[p] == j and (with_border or lab[i] < K)]
+
+    def order(key):
+        return sorted(range(n), key=lambda j: (key(j), j))
+
+    def with_border(j):
+        # R_B's rows counted as a part K; the split leaf from the highest
+        # differing bit, as a bitwise implementation would compute it
+        ps = parts_of(j, True)
+        if not ps:
+            return 2 * K
+        a, b = min(ps), max(ps)
+        if a == b:
+            return 2 * a
+        hb = (a ^ b).bit_length() - 1
+        return 2 * ((b >> hb) << hb) - 1
+
+    def lowest_part(j):
+        ps = parts_of(j, False)
+        return 2 * K if not ps else 2 * min(ps)
+
+    def untouched_inline(j):
+        ps = parts_of(j, False)
+        if not ps:
+            return -1
+        a, b = min(ps), max(ps)
+        return 2 * a if a == b else OO._between(a, b, K)
+
+    for wrong in (with_border, lowest_part, untouched_inline):
+        assert order(wrong) != s["col_perm"], wrong.__name__
