@@ -297,3 +297,23 @@ def test_column_increments_fall_back_on_wide_rows():
     st = _check(m, n, rp, ci, v, x, y_ref, row_perm=order,
                 flags=S.SPMV_FLAG_TILED_NATURAL | S.SPMV_FLAG_COL_DELTA)
     assert 0 <= st["delta_nnz"] < st["gathered_nnz"]
+
+
+@pytest.mark.parametrize("name", ["mesh160", "blocks16", "rmat15"])
+def test_nested_border_forms_from_the_partitioner(name):
+    """SB (column-net) and DB (enhanced row-column-net) partitions laid out
+    with the nested border order, through the tiled kernel in the natural
+    form, in every shape, with and without column increments."""
+    rp, ci, _ = MATRICES[name]()
+    m = n = len(rp) - 1
+    v = _integer(rp, ci, 31)
+    x = synth.integer_x(n, 32)
+    y_ref = _reference(m, n, rp, ci, v, x)
+    shapes = _shapes(S.SPMV_F64, 1, int(rp[-1]))
+    for method in (S.SPMV_PART_CN, S.SPMV_PART_ERCN):
+        part = S.spmv_partition(m, n, rp, ci, method, K=16, seed=0)
+        rperm, cperm = S.spmv_reorder(m, n, rp, ci, S.SPMV_ORDER_NESTED, 16, part["labels"])
+        for shape in SHAPE_NAMES:
+            for extra in (0, S.SPMV_FLAG_COL_DELTA):
+                _check(m, n, rp, ci, v, x, y_ref, row_perm=rperm, col_perm=cperm,
+                       **_with_flags(shapes[shape], S.SPMV_FLAG_TILED_NATURAL | extra))
